@@ -1,0 +1,346 @@
+"""Benchmark of the GB300 SDD mesh generator.
+
+One step = one whole mesh generation of the 257x257, 4x4-split ring workload
+(1521 interface nodes, 1e5 paths per node, dt = 1e-5, FP32 stepping with FP64
+accumulation, FP32 CG + FP64 refinement to 1e-10): the interface Monte Carlo
+(path kernel + per-node reduction) followed by the batched subdomain solves.
+Metric: SDE path-steps per second (whole job), with meshes/s beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands)
+on the host cores on a bounded sample of the same workload.
+Under torchrun each rank generates its own meshes (independent problems, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+# Algorithmic arithmetic operations of one FP32 path-step of the ring
+# density, counted per thread ("Roofline of the path kernel"):
+#   Philox4x32-10 / 2 steps: 10 rounds x (2 wide multiplies counted as 2,
+#   2 three-input xors, 2 key additions) = 60 -> 30 per step
+#   two uniforms (shift-or + add): 4;  Box-Muller pair: 10;  ring drift: 22;
+#   Euler-Maruyama update: 4;  exit test: 6;  step count and cap test: 2
+OPS_PER_STEP_RING_FP32 = 30 + 4 + 10 + 22 + 4 + 6 + 2        # = 78
+L2_BYTES = 129 * 1024 * 1024
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region
+    runs (every 200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_spec(name: str):
+    if name == "config1":
+        return W.config1()
+    if name == "config2":
+        return W.config2()
+    if name == "config4":
+        return W.config4()
+    raise ValueError(name)
+
+
+# ------------------------------------------------------------ CPU oracle ----
+def oracle_sample(spec, budget_s: float = 15.0, threads: int | None = None):
+    """Times the FP64 oracle on a bounded sample of `spec`: evenly spaced
+    interface nodes, the first paths of each node (the same Philox streams the
+    GPU runs), sized to about `budget_s` seconds on the host cores."""
+    import oracle
+    threads = threads or oracle.default_threads()
+    nodes = oracle.interface_nodes(spec.n, spec.sx, spec.sy)
+    E = oracle.bmap_tables(spec.n, spec.bmap_mode, spec.family, spec.coef_mode, spec.params)
+    k = max(threads, 1)
+    idx = np.linspace(0, len(nodes) - 1, k).round().astype(int)
+    # calibration: 32 paths per sampled node
+    t0 = time.perf_counter()
+    r = oracle.mc_nodes(spec.n, nodes[idx], E, spec.family, spec.coef_mode, spec.params,
+                        spec.seed, 32, spec.dt, spec.cap(), spec.tie(), node_ids=idx,
+                        threads=threads)
+    cal = time.perf_counter() - t0
+    paths = int(max(32, min(spec.paths, 32 * budget_s / max(cal, 1e-3))))
+    t0 = time.perf_counter()
+    r = oracle.mc_nodes(spec.n, nodes[idx], E, spec.family, spec.coef_mode, spec.params,
+                        spec.seed, paths, spec.dt, spec.cap(), spec.tie(), node_ids=idx,
+                        threads=threads)
+    el = time.perf_counter() - t0
+    steps = int(r["steps"].sum())
+    return {"value": steps / el, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+            "sample": "%d of %d interface nodes x %d paths (FP64, %d path-steps, %.1f s)"
+                      % (len(idx), len(nodes), paths, steps, el),
+            "seconds": el, "path_steps": steps}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    spec = make_spec(args.config)
+    threads = oracle.default_threads()
+    for _ in range(args.warmup):
+        oracle_sample(spec, budget_s=2.0, threads=threads)
+    vals, secs, steps = [], 0.0, 0
+    for _ in range(args.steps):
+        s = oracle_sample(spec, budget_s=args.ref_budget, threads=threads)
+        vals.append(s["value"])
+        secs += s["seconds"]
+        steps += s["path_steps"]
+    value = steps / secs
+    line = {"impl": "reference", "metric": "SDE path-steps/s", "value": value,
+            "unit": "path-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": spec.label, "sample": s["sample"]},
+            "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads,
+                             "kind": "oracle", "sample": s["sample"]},
+            "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm ----
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1310_3435_gb300 import native as N
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = make_spec(args.config)
+    # independent problem per rank: its own seed (weak scaling, no collective)
+    spec = W.MeshSpec(**{**spec.__dict__, "seed": spec.seed + 1000003 * rank})
+    stream = torch.cuda.Stream(device=dev)
+    plan = N.Plan(spec)
+    mc = plan.mc_params(precision=spec.precision if args.precision is None else args.precision)
+    sp = plan.solve_params()
+    n = spec.n
+    mesh = torch.zeros((n, n, 2), dtype=torch.float64, device=dev)
+    mean = torch.zeros((plan.n_nodes, 2), dtype=torch.float64, device=dev)
+    se = torch.zeros((plan.n_nodes, 2), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        N.sdd_interface_mc(plan.handle, mc, mean, se, want_stats=False, stream=stream)
+        if evs:
+            evs[1].record(stream)
+        N.sdd_subdomain_solve(plan.handle, mean, sp, mesh, want_stats=False, stream=stream)
+        if evs:
+            evs[2].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+            flush.zero_()
+    torch.cuda.synchronize()
+    mc_stats = N.sdd_plan_last_mc_stats(plan.handle)
+    path_steps = int(mc_stats.path_steps)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    launches0 = N.sdd_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_begin = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_begin.record(stream)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            step(evs[k])
+            flush.zero_()                      # L2 flush between timed steps
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = N.sdd_kernel_launches() - launches0
+    ms_mc = [e[0].elapsed_time(e[1]) for e in evs]
+    ms_solve = [e[1].elapsed_time(e[2]) for e in evs]
+    ms_step = [a + b for a, b in zip(ms_mc, ms_solve)]
+    t_total = sum(ms_step) / 1000.0
+    check = N.sdd_plan_last_mc_stats(plan.handle)
+    assert int(check.path_steps) == path_steps
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = world * path_steps * args.steps / t_total
+    meshes_per_s = world * args.steps / t_total
+
+    # end to end through the public API with host buffers: plan (H2D of the
+    # request's tables) + mesh generation + D2H of mesh and interface values
+    e2e = None
+    if not args.no_e2e:
+        mesh_h = np.zeros((n, n, 2))
+        mean_h = np.zeros((plan.n_nodes, 2))
+        se_h = np.zeros((plan.n_nodes, 2))
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            with N.Plan(spec) as P2:
+                N.sdd_mesh_generate(P2.handle, mc, sp, mesh_h, mean_h, se_h, want_stats=False,
+                                    stream=stream)
+        el = time.perf_counter() - t0
+        h2d = plan.n_nodes * 2 * 4 + 8 * n * 8
+        d2h = mesh_h.nbytes + mean_h.nbytes + se_h.nbytes
+        e2e = {"value": world * path_steps * e2e_steps / el, "unit": "path-steps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "meshes_per_s": world * e2e_steps / el}
+
+    peaks, peak_kind = measured_peaks()
+    sm_clock_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * 128 * sm_clock_max * 1e6 / 1e9          # Gop/s
+    t_mc = sum(ms_mc) / len(ms_mc) / 1000.0
+    achieved = OPS_PER_STEP_RING_FP32 * path_steps / t_mc / 1e9
+    line = {
+        "metric": "SDE path-steps/s",
+        "step": "one whole mesh generation: interface Monte Carlo + subdomain solves",
+        "value": value, "unit": "path-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-step/f64-acc" if mc.precision == N.SDD_FP32_STEP else "f64",
+        "data": "synthetic",
+        "config": {"workload": spec.label, "n": n, "split": [spec.sx, spec.sy],
+                   "interface_nodes": plan.n_nodes, "paths_per_node": spec.paths,
+                   "dt": spec.dt, "path_steps_per_mesh": path_steps,
+                   "l2": "flushed between timed steps (2x L2 write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "meshes_per_s": meshes_per_s,
+        "ms_interface_mc": float(np.mean(ms_mc)), "ms_subdomain_solve": float(np.mean(ms_solve)),
+        "max_stderr": float(mc_stats.max_stderr),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_paths<FP32> (+k_reduce)",
+                     "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
+                                   % (sms, sm_clock_max, peak_kind),
+                     "ops_per_path_step": OPS_PER_STEP_RING_FP32},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = {k: v for k, v in oracle_sample(spec, budget_s=args.ref_budget).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--config", default="config2", choices=["config1", "config2", "config4"])
+    ap.add_argument("--precision", type=int, default=None, help="0 FP64, 1 FP32 stepping")
+    ap.add_argument("--ref-budget", type=float, default=15.0,
+                    help="seconds of CPU work per oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

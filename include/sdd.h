@@ -1,0 +1,224 @@
+/*
+ * sdd.h - C ABI of the GB300 stochastic-deterministic domain decomposition
+ * (SDD) mesh generator: Monte Carlo evaluation of the Feynman-Kac
+ * representation of the linear Winslow generator at subdomain-interface nodes,
+ * followed by independent Dirichlet solves on the subdomains.
+ *
+ * Method: Bihlo & Haynes, "Parallel stochastic methods for PDE based grid
+ * generation" (arXiv 1310.3435).
+ *   - generator  -div(c grad u) = 0 on the unit square, u = boundary map on the
+ *     boundary (eq. WinslowTypeGridGenerator, §2.1); c = w or c = 1/w;
+ *   - u(x) = E[boundary map at the first exit point of X]  (eq. ...StochasticSolutionA)
+ *     for dX = grad(ln c) dt + sqrt(2) dW (eq. ...StochasticSolutionB, with the
+ *     noise scale fixed by the expanded form, eq. ...Expanded);
+ *   - Euler-Maruyama with time step dt and an exit test at the end of each
+ *     step (§2.2); sample mean over N paths per node, error ~ N^-1/2 (§2.2);
+ *   - interface values as Dirichlet data for independent subdomain solves,
+ *     no iteration between subdomains (§2.1, Fig. 1; §3.5); conservative
+ *     centred differences on a uniform grid (§3.2).
+ *
+ * Conventions (all entry points):
+ *   - Return SDD_OK (0) on success, a negative SDD_ERR_* code on failure;
+ *     sdd_last_error() then gives a message (thread-local, valid until the
+ *     next call on the same thread).
+ *   - Grid: n x n nodes (s_i, t_j) = (i, j)/(n-1).  Mesh arrays are
+ *     [n][n][2] doubles indexed [j][i][comp] (row j = t index), comp 0 = u1
+ *     (the s-like coordinate), comp 1 = u2.
+ *   - Interface nodes: the interior nodes (1 <= i, j <= n-2) on the interface
+ *     lines i in I_x or j in I_y, I_k = round(k (n-1)/s) (halves up), each
+ *     node once, ordered by j then i.  Per-node arrays are [n_nodes][2].
+ *   - Output and input arrays are owned by the caller.  A pointer is device
+ *     memory if cudaPointerGetAttributes reports a device or managed
+ *     allocation, else host memory.  With device pointers a call is
+ *     asynchronous and ordered on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream); with any host pointer among its outputs it copies and
+ *     synchronises `stream` before returning.
+ *   - A plan owns device buffers on the device that was current when it was
+ *     created; calls must be made with that device current.  A plan is not
+ *     thread-safe; concurrent calls on different plans are.
+ */
+#ifndef SDD_H
+#define SDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SDD_OK                  0
+#define SDD_ERR_INVALID_ARG   (-1)
+#define SDD_ERR_OOM           (-2)
+#define SDD_ERR_CUDA          (-3)
+#define SDD_ERR_NOT_CONVERGED (-4)
+#define SDD_ERR_NO_DEVICE     (-5)
+
+/* ---- density families (shapes of the paper's monitor functions) ---- */
+/* BUMPS: params = [nb, (A, cs, ct, ks, kt) x nb], nb <= 6:
+ *        w = 1 + sum A exp(-ks (s-cs)^2 - kt (t-ct)^2)   (eq. MonitorFunctionRunningExample)
+ * RING : params = [A, cs, ct, k, r0]:
+ *        w = 1 + A sech^2(k (|x - c| - r0))             (ring of eq. FiveRingMonitorFunction)
+ * RIDGE: params = [A, k, t0, a, f]:
+ *        w = 1 + A exp(-k (t - t0 - a sin(2 pi f s))^2)  (eq. MackenzieMonitorFunction) */
+#define SDD_FAMILY_BUMPS 0
+#define SDD_FAMILY_RING  1
+#define SDD_FAMILY_RIDGE 2
+#define SDD_MAX_BUMPS    6
+#define SDD_MAX_PARAMS   32
+
+/* coefficient of the generator: c = w (the paper's eq. as printed) or c = 1/w */
+#define SDD_COEF_W     0
+#define SDD_COEF_INV_W 1
+
+/* boundary map u|boundary:
+ *   IDENTITY : u = (s, t)
+ *   PAPER_1D : u1 = 0 on s=0, 1 on s=1; u2 = 0 on t=0, 1 on t=1; u1 on t=0,1 and
+ *              u2 on s=0,1 from the 1D generator -(c u')' = 0 discretised by
+ *              the conservative three-point difference (§3.2)
+ *   TABLE    : caller's tables edges[2 comps][4 edges][n] (host pointer), edge
+ *              0 bottom (t=0, along s), 1 top (t=1), 2 left (s=0, along t),
+ *              3 right (s=1).  Rows t=0 and t=1 take the bottom/top tables,
+ *              corners included. */
+#define SDD_BMAP_IDENTITY 0
+#define SDD_BMAP_PAPER_1D 1
+#define SDD_BMAP_TABLE    2
+
+/* path precision: FP64 stepping, or FP32 stepping with FP64 exit-point
+ * interpolation and compensated FP64 per-node sums */
+#define SDD_FP64      0
+#define SDD_FP32_STEP 1
+
+/* subdomain solvers */
+#define SDD_SOLVER_SOR            0   /* FP64 red-black SOR */
+#define SDD_SOLVER_CG_FP32_REFINE 1   /* FP32 Jacobi-PCG inner solves + FP64 iterative refinement */
+
+typedef struct sdd_plan sdd_plan;
+
+typedef struct {
+    int32_t family;                    /* SDD_FAMILY_* */
+    int32_t coef_mode;                 /* SDD_COEF_* */
+    int32_t n_params;                  /* used entries of params */
+    int32_t reserved;
+    double params[SDD_MAX_PARAMS];
+} sdd_density;
+
+typedef struct {
+    int32_t mode;                      /* SDD_BMAP_* */
+    int32_t reserved;
+    const double* edges;               /* host [2][4][n] for SDD_BMAP_TABLE, else NULL */
+} sdd_bmap;
+
+typedef struct {
+    uint64_t paths_per_node;           /* N >= 2, < 2^32 */
+    double dt;                         /* Euler-Maruyama step, > 0 */
+    uint64_t seed;                     /* Philox4x32-10 key (lo, hi words) */
+    int32_t precision;                 /* SDD_FP64 | SDD_FP32_STEP */
+    int32_t chunk;                     /* paths per work item, 0 = automatic */
+    uint64_t max_steps;                /* step cap per path, 0 = ceil(2/dt) */
+    double tie_delta;                  /* <0: default (1e-11 FP64, 0 FP32) */
+} sdd_mc_params;
+
+typedef struct {
+    uint64_t paths;                    /* paths run, all nodes */
+    uint64_t path_steps;               /* Euler-Maruyama updates, counted exactly */
+    uint64_t ties;                     /* paths flagged as exit-decision ties */
+    uint64_t non_exits;                /* paths stopped by the step cap */
+    double max_stderr;                 /* largest per-node standard error */
+} sdd_mc_stats;
+
+/* Per-node sums, d = F - X0 (score minus start point), all paths and the
+ * paths not flagged as ties ("nt"). */
+typedef struct {
+    double sum[2];
+    double sumsq[2];
+    double sum_nt[2];
+    double sumsq_nt[2];
+    uint64_t paths;
+    uint64_t ties;
+    uint64_t non_exits;
+    uint64_t steps;
+} sdd_node_sums;
+
+typedef struct {
+    int32_t solver;                    /* SDD_SOLVER_* */
+    int32_t max_iter;                  /* sweeps (SOR) or inner iterations (CG); 0 = default */
+    double tol;                        /* relative residual ||b - A u||_2 / ||b||_2 per subdomain */
+    double omega;                      /* SOR relaxation; 0 = per-subdomain estimate */
+} sdd_solve_params;
+
+typedef struct {
+    int32_t converged;                 /* subdomains that met tol */
+    int32_t subdomains;
+    int32_t max_iterations;            /* largest iteration count over subdomains */
+    int32_t reserved;
+    double max_rel_residual;           /* largest final relative residual */
+} sdd_solve_stats;
+
+/* Builds a plan for an n x n grid split sx x sy (2 <= ... see below) with
+ * density `dens` and boundary map `bmap`: enumerates the interface nodes,
+ * builds the boundary tables and copies them to the current device.
+ * Requires 3 <= n <= 16385, 1 <= sx, sy <= n-1.  *out receives the plan.
+ * Errors: INVALID_ARG (sizes, unknown family/mode, nb > SDD_MAX_BUMPS, NULL),
+ * OOM, CUDA, NO_DEVICE.  Paper: §2.1, Fig. 1 (interfaces); §3.2 (boundary map). */
+int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap* bmap,
+                  sdd_plan** out);
+
+/* Number of unique interface nodes of the plan. */
+int sdd_plan_num_nodes(const sdd_plan* plan, int64_t* n_nodes);
+
+/* Copies the interface nodes' (i, j) indices, host int32 [n_nodes][2]. */
+int sdd_plan_nodes(const sdd_plan* plan, int32_t* ij);
+
+/* Copies the plan's boundary tables, host double [2][4][n]. */
+int sdd_plan_edges(const sdd_plan* plan, double* edges);
+
+/* Monte Carlo estimate at every interface node (§2.2): N paths per node,
+ * Euler-Maruyama steps, exit test at the end of each step, score by linear
+ * interpolation of the boundary tables at the segment/side intersection,
+ * sample mean and standard error.  Path p of node m draws its normals from
+ * Philox4x32-10(key = seed, counter = (step/2, p, m, 0)), Box-Muller.
+ * mean, stderr_: [n_nodes][2] (either may be NULL); stats: host or NULL.
+ * Errors: INVALID_ARG (N < 2, N >= 2^32, dt <= 0, bad precision), OOM, CUDA. */
+int sdd_interface_mc(sdd_plan* plan, const sdd_mc_params* mc, double* mean, double* stderr_,
+                     sdd_mc_stats* stats, void* stream);
+
+/* Same paths as sdd_interface_mc; returns the per-node sums instead
+ * (host or device array of n_nodes sdd_node_sums). */
+int sdd_interface_mc_sums(sdd_plan* plan, const sdd_mc_params* mc, sdd_node_sums* sums,
+                          void* stream);
+
+/* Statistics of the plan's last Monte Carlo call (synchronises its stream). */
+int sdd_plan_last_mc_stats(sdd_plan* plan, sdd_mc_stats* stats);
+
+/* Subdomain solves (§2.1, §3.5): the interface values `iface` ([n_nodes][2],
+ * host or device) and the boundary map are Dirichlet data; each subdomain's
+ * conservative five-point system sum_nbr c_edge (u_nbr - u_ij) = 0, c at edge
+ * midpoints (§3.2), is solved independently.  Writes the whole mesh
+ * [n][n][2] (boundary, interfaces and interiors) to `mesh`.  stats: host or
+ * NULL; when given, returns SDD_ERR_NOT_CONVERGED if a subdomain missed tol
+ * (the mesh is still written).  Errors: INVALID_ARG, OOM, CUDA. */
+int sdd_subdomain_solve(sdd_plan* plan, const double* iface, const sdd_solve_params* sp,
+                        double* mesh, sdd_solve_stats* stats, void* stream);
+
+/* Interface Monte Carlo followed by the subdomain solves, all on `stream`
+ * with the interface values kept on the device.  Outputs (each may be NULL
+ * except mesh): mesh [n][n][2], iface_mean / iface_stderr [n_nodes][2]. */
+int sdd_mesh_generate(sdd_plan* plan, const sdd_mc_params* mc, const sdd_solve_params* sp,
+                      double* mesh, double* iface_mean, double* iface_stderr,
+                      sdd_mc_stats* mc_stats, sdd_solve_stats* solve_stats, void* stream);
+
+/* Frees the plan and its device buffers (synchronises its last stream). */
+void sdd_plan_destroy(sdd_plan* plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sdd_last_error(void);
+
+/* Number of kernels this library has launched in the process so far. */
+int sdd_kernel_launches(uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDD_H */

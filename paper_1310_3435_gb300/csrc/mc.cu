@@ -1,0 +1,726 @@
+// Interface Monte Carlo of the SDD mesh generator (Bihlo & Haynes, §2.1-2.2):
+// Euler-Maruyama paths of dX = grad(ln c) dt + sqrt(2) dW from each interface
+// node, exit test at the end of each step, score = boundary map at the exit
+// point (linear interpolation of the per-edge tables), per-node sums.
+//
+// Work decomposition.  A work item is one chunk of `chunk` consecutive paths
+// of one node of one mesh.  A persistent grid of warps pulls items from an
+// atomic counter; inside an item the 32 lanes each run one path and, when
+// paths exit, the freed lanes take the next paths of the item in lane order
+// (ballot + popc), so lanes stay busy until the item runs dry.  The
+// assignment of paths to lanes depends only on the item, so every item's
+// sums, and the per-node sums built from them in chunk order, are bitwise
+// reproducible whatever the launch order or the other meshes in a batch.
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
+// counter = (step/2, path, node, 0); one call gives the four normals of two
+// consecutive steps by the Box-Muller transform.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "sdd_internal.h"
+
+namespace sdd {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MC_THREADS = 256;
+// Minimum resident blocks per SM requested from the register allocator: the
+// FP32-stepping kernel fits 80 registers without spills at 3 blocks of 256.
+#ifndef SDD_MC_MIN_BLOCKS_F32
+#define SDD_MC_MIN_BLOCKS_F32 3
+#endif
+#ifndef SDD_MC_MIN_BLOCKS_F64
+#define SDD_MC_MIN_BLOCKS_F64 1
+#endif
+
+// ------------------------------------------------------------- Philox ----
+// Philox4x32-10: ten rounds of two 32x32->64 multiplies (multipliers M0, M1)
+// and a Feistel-like xor/permute, the key bumped by (W0, W1) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
+        const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
+        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+        k0 += W0;
+        k1 += W1;
+    }
+    return x;
+}
+
+// ------------------------------------------ fast FP32 hardware approximations
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float TWO_PI_F = 6.28318530717958647692f;
+constexpr double PI_D = 3.14159265358979323846;
+constexpr float LN2_X2_F = 1.38629436111989061883f;    // 2 ln 2
+
+// Box-Muller, FP32.  Uniforms U = (floor(r / 2^9) + 1/2) 2^-23 are exact in
+// FP32 and lie in (0,1); the angle 2 pi U is taken as 2 pi (U - 1/2) + pi,
+// i.e. (cos, sin)(2 pi U) = -(cos, sin)(2 pi (U - 1/2)), which keeps the
+// argument of the hardware sine/cosine in [-pi, pi].
+__device__ __forceinline__ float uniform23(uint32_t r)
+{
+    // 1 + floor(r/2^9) 2^-23 in [1,2), minus (1 - 2^-24): exact.
+    return __uint_as_float((r >> 9) | 0x3f800000u) - 0.99999994039535522461f;
+}
+
+__device__ __forceinline__ void box_muller_f32(uint32_t ra, uint32_t rb, float& z0, float& z1)
+{
+    const float ua = uniform23(ra), ub = uniform23(rb);
+    const float v = -LN2_X2_F * lg2_approx(ua);            // -2 ln ua > 0
+    const float R = v * rsqrt_approx(v);
+    const float ang = TWO_PI_F * (ub - 0.5f);
+    z0 = -R * cos_approx(ang);
+    z1 = -R * sin_approx(ang);
+}
+
+// Box-Muller, FP64 with CUDA's double-precision log / sqrt / sincospi.
+__device__ __forceinline__ void box_muller_f64(uint32_t ra, uint32_t rb, double& z0, double& z1)
+{
+    const double ua = ((double)ra + 0.5) * 0x1p-32;
+    const double ub = ((double)rb + 0.5) * 0x1p-32;
+    const double R = sqrt(-2.0 * log(ua));
+    double s, c;
+    sincospi(2.0 * ub, &s, &c);
+    z0 = R * c;
+    z1 = R * s;
+}
+
+// ----------------------------------------------------- densities, FP32 ----
+// Each returns b = grad ln c at (s, t), c = w^sgn.
+// BUMPS: pf[8b..8b+6] = A, cs, ct, ks log2 e, kt log2 e, -2 ks, -2 kt.
+template <int NB>
+struct BumpsF32 {
+    float p[NB][7];
+    float sgn;
+    __device__ void load(const MeshDev& M)
+    {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) p[b][q] = M.pf[8 * b + q];
+        sgn = (float)M.sgn;
+    }
+    __device__ __forceinline__ void drift(float s, float t, float& bs, float& bt) const
+    {
+        float w = 1.0f, gs = 0.0f, gt = 0.0f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float ds = s - p[b][1], dtt = t - p[b][2];
+            const float ex = -fmaf(p[b][3] * ds, ds, p[b][4] * dtt * dtt);
+            const float e = p[b][0] * ex2_approx(ex);
+            w += e;
+            gs = fmaf(e * p[b][5], ds, gs);
+            gt = fmaf(e * p[b][6], dtt, gt);
+        }
+        const float inv = sgn * rcp_approx(w);
+        bs = gs * inv;
+        bt = gt * inv;
+    }
+};
+
+// RING: pf = cs, ct, r0, -2 k log2 e, 4 A, sgn * (-8 A k).
+// With e = exp(-2|u|), u = k (r - r0):  (dw/dr) / w = -8 A k sign(u) e (1 - e)
+// / ((1 + e)((1 + e)^2 + 4 A e)), and b = sgn (dw/dr)/w (s - cs, t - ct)/r.
+struct RingF32 {
+    float cs, ct, r0, c1, A4, K;
+    __device__ void load(const MeshDev& M)
+    {
+        cs = M.pf[0]; ct = M.pf[1]; r0 = M.pf[2]; c1 = M.pf[3]; A4 = M.pf[4]; K = M.pf[5];
+    }
+    __device__ __forceinline__ void drift(float s, float t, float& bs, float& bt) const
+    {
+        const float ds = s - cs, dtt = t - ct;
+        const float r2 = fmaf(ds, ds, dtt * dtt);
+        const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
+        const float u = fmaf(r2, rinv, -r0);
+        const float e = ex2_approx(c1 * fabsf(u));
+        const float ope = 1.0f + e;
+        const float D = ope * fmaf(ope, ope, A4 * e);
+        const float num = K * copysignf(e * (1.0f - e), u) * rinv;
+        const float f = num * rcp_approx(D);
+        bs = f * ds;
+        bt = f * dtt;
+    }
+};
+
+// RIDGE: pf = A, k log2 e, t0, a, f, -2 k, -2 pi a f.
+// v = t - t0 - a sin(2 pi f s); w = 1 + A exp(-k v^2);
+// dw/dt = e (-2 k v), dw/ds = dw/dt (-2 pi a f cos(2 pi f s)).
+struct RidgeF32 {
+    float A, kl, t0, a, f, m2k, m2paf, sgn;
+    __device__ void load(const MeshDev& M)
+    {
+        A = M.pf[0]; kl = M.pf[1]; t0 = M.pf[2]; a = M.pf[3]; f = M.pf[4];
+        m2k = M.pf[5]; m2paf = M.pf[6]; sgn = (float)M.sgn;
+    }
+    __device__ __forceinline__ void drift(float s, float t, float& bs, float& bt) const
+    {
+        const float fr = f * s;
+        const float x = TWO_PI_F * (fr - rintf(fr));           // in [-pi, pi]
+        const float sn = sin_approx(x), cn = cos_approx(x);
+        const float v = t - t0 - a * sn;
+        const float e = A * ex2_approx(-kl * v * v);
+        const float inv = sgn * rcp_approx(1.0f + e);
+        const float gt = e * m2k * v;
+        bt = gt * inv;
+        bs = gt * (m2paf * cn) * inv;
+    }
+};
+
+// ----------------------------------------------------- densities, FP64 ----
+struct BumpsF64 {
+    const double* p;
+    int nb;
+    double sgn;
+    __device__ void load(const MeshDev& M) { p = M.pd; nb = M.nb; sgn = M.sgn; }
+    __device__ __forceinline__ void drift(double s, double t, double& bs, double& bt) const
+    {
+        double w = 1.0, gs = 0.0, gt = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double* q = p + 1 + 5 * b;
+            const double A = q[0], cs = q[1], ct = q[2], ks = q[3], kt = q[4];
+            const double ds = s - cs, dtt = t - ct;
+            const double e = A * exp(-(ks * ds * ds + kt * dtt * dtt));
+            w += e;
+            gs += e * (-2.0 * ks * ds);
+            gt += e * (-2.0 * kt * dtt);
+        }
+        bs = sgn * gs / w;
+        bt = sgn * gt / w;
+    }
+};
+
+struct RingF64 {
+    double A, cs, ct, k, r0, sgn;
+    __device__ void load(const MeshDev& M)
+    {
+        A = M.pd[0]; cs = M.pd[1]; ct = M.pd[2]; k = M.pd[3]; r0 = M.pd[4]; sgn = M.sgn;
+    }
+    __device__ __forceinline__ void drift(double s, double t, double& bs, double& bt) const
+    {
+        const double ds = s - cs, dtt = t - ct;
+        const double r = sqrt(ds * ds + dtt * dtt);
+        if (r == 0.0) { bs = 0.0; bt = 0.0; return; }
+        const double u = k * (r - r0);
+        const double e = exp(-2.0 * fabs(u));
+        const double ope = 1.0 + e;
+        const double D = ope * (ope * ope + 4.0 * A * e);
+        const double g = sgn * (-8.0 * A * k) * copysign(e * (1.0 - e), u) / (D * r);
+        bs = g * ds;
+        bt = g * dtt;
+    }
+};
+
+struct RidgeF64 {
+    double A, k, t0, a, f, sgn;
+    __device__ void load(const MeshDev& M)
+    {
+        A = M.pd[0]; k = M.pd[1]; t0 = M.pd[2]; a = M.pd[3]; f = M.pd[4]; sgn = M.sgn;
+    }
+    __device__ __forceinline__ void drift(double s, double t, double& bs, double& bt) const
+    {
+        double sn, cn;
+        sincospi(2.0 * f * s, &sn, &cn);
+        const double v = t - t0 - a * sn;
+        const double e = A * exp(-k * v * v);
+        const double w = 1.0 + e;
+        const double gt = e * (-2.0 * k * v);
+        const double gs = gt * (-2.0 * PI_D * a * f * cn);
+        bs = sgn * gs / w;
+        bt = sgn * gt / w;
+    }
+};
+
+// ------------------------------------------------------ exit and score ----
+// Edge crossed by the step x -> y (some coordinate of y outside (0,1)) and the
+// tangential coordinate of the exit point: for each violated side
+// theta = (x_d - side) / (x_d - y_d); the smallest theta wins, an exact tie
+// going to the s-sides; the tangential coordinate is clamped to [0,1].
+// Edges: 0 bottom (t=0), 1 top (t=1), 2 left (s=0), 3 right (s=1).
+template <typename R>
+__device__ __forceinline__ int exit_edge(R xs, R xt, R ys, R yt, R& tau)
+{
+    int es = -1, et = -1;
+    R ths = R(2), tht = R(2);
+    if (ys <= R(0)) { es = 2; ths = xs / (xs - ys); }
+    else if (ys >= R(1)) { es = 3; ths = (xs - R(1)) / (xs - ys); }
+    if (yt <= R(0)) { et = 0; tht = xt / (xt - yt); }
+    else if (yt >= R(1)) { et = 1; tht = (xt - R(1)) / (xt - yt); }
+    if (es >= 0 && (et < 0 || ths <= tht)) {
+        tau = fmin(fmax(xt + ths * (yt - xt), R(0)), R(1));
+        return es;
+    }
+    tau = fmin(fmax(xs + tht * (ys - xs), R(0)), R(1));
+    return et;
+}
+
+// Nearest side of an interior point (first minimum in the order s=0, s=1,
+// t=0, t=1) and the tangential coordinate of its projection; used for paths
+// stopped by the step cap.
+template <typename R>
+__device__ __forceinline__ int nearest_edge(R s, R t, R& tau)
+{
+    R d = s;
+    int e = 2;
+    tau = t;
+    if (R(1) - s < d) { d = R(1) - s; e = 3; }
+    if (t < d) { d = t; e = 0; tau = s; }
+    if (R(1) - t < d) { e = 1; tau = s; }
+    return e;
+}
+
+// Linear interpolation in a table of n values at tau_j = j/(n-1), in FP64.
+__device__ __forceinline__ double lookup(const double* __restrict__ T, int n, double tau)
+{
+    const double x = tau * (double)(n - 1);
+    int j = (int)floor(x);
+    j = min(max(j, 0), n - 2);
+    const double fr = x - (double)j;
+    const double a = __ldg(T + j), b = __ldg(T + j + 1);
+    return a + fr * (b - a);
+}
+
+// --------------------------------------------------- compensated sums ----
+__device__ __forceinline__ void two_sum_add(double& hi, double& lo, double x)
+{
+    const double s = hi + x;
+    const double bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+// Per-lane accumulators live in shared memory (they are touched once per
+// path, not per step), one column per thread, so the step loop keeps only the
+// path state in registers.
+struct AccSmem {
+    double v[12][MC_THREADS];   // s_hi[2] s_lo[2] q_hi[2] q_lo[2] st[2] qt[2]
+};
+
+__device__ __forceinline__ void acc_zero(AccSmem& A, int tid)
+{
+#pragma unroll
+    for (int q = 0; q < 12; ++q) A.v[q][tid] = 0.0;
+}
+
+// Adds d = F - X0 of one path: compensated sums over non-tie paths, plain sums
+// over tie-flagged paths.
+__device__ __forceinline__ void acc_add(AccSmem& A, int tid, double d0, double d1, bool tie)
+{
+    if (!tie) {
+        double h, l;
+        h = A.v[0][tid]; l = A.v[2][tid]; two_sum_add(h, l, d0); A.v[0][tid] = h; A.v[2][tid] = l;
+        h = A.v[1][tid]; l = A.v[3][tid]; two_sum_add(h, l, d1); A.v[1][tid] = h; A.v[3][tid] = l;
+        h = A.v[4][tid]; l = A.v[6][tid]; two_sum_add(h, l, d0 * d0); A.v[4][tid] = h; A.v[6][tid] = l;
+        h = A.v[5][tid]; l = A.v[7][tid]; two_sum_add(h, l, d1 * d1); A.v[5][tid] = h; A.v[7][tid] = l;
+    } else {
+        A.v[8][tid] += d0;
+        A.v[9][tid] += d1;
+        A.v[10][tid] += d0 * d0;
+        A.v[11][tid] += d1 * d1;
+    }
+}
+
+// Butterfly over the warp of the lane sums; lane 0 writes the item's slot.
+__device__ void acc_write_slot(const AccSmem& A, int tid, int lane, uint32_t ties, uint32_t caps,
+                               unsigned long long steps, Slot* __restrict__ out)
+{
+    double v[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) v[q] = A.v[q][tid];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // (hi, lo) pairs: (v[q], v[q + 2]) for q = 0, 1 and (v[q + 2], v[q + 4]) for q = 2, 3
+            const int hq = q < 2 ? q : q + 2, lq = hq + 2;
+            const double oh = __shfl_xor_sync(FULL, v[hq], off);
+            const double ol = __shfl_xor_sync(FULL, v[lq], off);
+            v[lq] += ol;
+            two_sum_add(v[hq], v[lq], oh);
+        }
+#pragma unroll
+        for (int q = 8; q < 12; ++q) v[q] += __shfl_xor_sync(FULL, v[q], off);
+        ties += __shfl_xor_sync(FULL, ties, off);
+        caps += __shfl_xor_sync(FULL, caps, off);
+        steps += __shfl_xor_sync(FULL, steps, off);
+    }
+    if (lane == 0) {
+        Slot sl;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            sl.s_hi[c] = v[c]; sl.s_lo[c] = v[2 + c];
+            sl.q_hi[c] = v[4 + c]; sl.q_lo[c] = v[6 + c];
+            sl.st[c] = v[8 + c]; sl.qt[c] = v[10 + c];
+        }
+        sl.ties = ties;
+        sl.caps = caps;
+        sl.steps = steps;
+        *out = sl;
+    }
+}
+
+template <int PREC> struct RealOf { using T = double; };
+template <> struct RealOf<SDD_FP32_STEP> { using T = float; };
+
+// ------------------------------------------------------- one work item ----
+// Runs the paths of chunk `chunk` of node `node`; lanes refill from the chunk
+// in lane order as their paths end.  Two Euler-Maruyama steps per Philox call.
+template <int PREC, class Dens>
+__device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uint32_t node,
+                                         uint32_t chunk, Slot* __restrict__ out, AccSmem& A,
+                                         int tid, int lane)
+{
+    using R = typename RealOf<PREC>::T;
+    const int n = M.n;
+    const int2 ij = M.nodes[node];
+    const double s0d = (double)ij.x / (double)(n - 1);
+    const double t0d = (double)ij.y / (double)(n - 1);
+    const R s0 = (R)s0d, t0 = (R)t0d;
+    const R dtR = (R)M.dt, sq = (R)M.sqrt2dt;
+    const R delta = (R)M.tie_delta;
+    const uint32_t kmax = M.max_steps;
+    const uint32_t key0 = M.key0, key1 = M.key1;
+    const uint32_t p_begin = chunk * M.chunk;
+    const uint32_t p_end = min(M.paths, p_begin + M.chunk);
+
+    uint32_t path = p_begin + (uint32_t)lane;
+    bool active = path < p_end;
+    uint32_t cursor = p_begin + 32u;
+    R xs = s0, xt = t0;      // position before the current step
+    R ys = s0, yt = t0;      // position after it
+    uint32_t k = 0;
+    bool tie = false;
+    uint32_t ties = 0, caps = 0;
+    unsigned long long steps = 0;
+    acc_zero(A, tid);
+    __syncwarp();
+
+    // One Euler-Maruyama step from (xs, xt) with normals (za, zb) into
+    // (ys, yt).  Returns 0 to continue, 1 on exit, 2 at the step cap.
+    auto step = [&](R za, R zb) -> int {
+        R bs, bt;
+        dens.drift(xs, xt, bs, bt);
+        ys = xs + bs * dtR + sq * za;
+        yt = xt + bt * dtR + sq * zb;
+        ++k;
+        if constexpr (PREC == SDD_FP64) {
+            const R m = fmin(fmin(fabs(ys), fabs(R(1) - ys)), fmin(fabs(yt), fabs(R(1) - yt)));
+            tie = tie || (m < delta);
+        }
+        if ((ys <= R(0)) | (ys >= R(1)) | (yt <= R(0)) | (yt >= R(1))) return 1;
+        if (k >= kmax) return 2;
+        xs = ys;
+        xt = yt;
+        return 0;
+    };
+
+    for (;;) {
+        int ended = 0;
+        if (active) {
+            const uint4 r = philox4x32_10(make_uint4(k >> 1, path, node, 0u), key0, key1);
+            R z0, z1, z2, z3;
+            if constexpr (PREC == SDD_FP64) {
+                box_muller_f64(r.x, r.y, z0, z1);
+                box_muller_f64(r.z, r.w, z2, z3);
+            } else {
+                box_muller_f32(r.x, r.y, z0, z1);
+                box_muller_f32(r.z, r.w, z2, z3);
+            }
+            ended = step(z0, z1);
+            if (!ended) ended = step(z2, z3);
+            if (ended) {
+                R tau;
+                const int e = ended == 1 ? exit_edge<R>(xs, xt, ys, yt, tau)
+                                         : nearest_edge<R>(ys, yt, tau);
+                const double td = (double)tau;
+                const double f0 = lookup(M.edges + (size_t)e * n, n, td);
+                const double f1 = lookup(M.edges + (size_t)(4 + e) * n, n, td);
+                acc_add(A, tid, f0 - s0d, f1 - t0d, tie);
+                ties += tie ? 1u : 0u;
+                caps += ended == 2 ? 1u : 0u;
+                steps += k;
+            }
+        }
+        const unsigned dm = __ballot_sync(FULL, ended != 0);
+        if (dm) {
+            if (ended) {
+                const unsigned rank = __popc(dm & ((1u << lane) - 1u));
+                path = cursor + rank;
+                active = path < p_end;
+                xs = s0;
+                xt = t0;
+                k = 0;
+                tie = false;
+            }
+            cursor += (uint32_t)__popc(dm);
+        }
+        if (!__any_sync(FULL, active)) break;
+    }
+    __syncwarp();
+    acc_write_slot(A, tid, lane, ties, caps, steps, out);
+    __syncwarp();
+}
+
+template <int PREC, class Dens>
+__device__ __forceinline__ void run_with(const MeshDev& M, uint32_t node, uint32_t chunk,
+                                         Slot* out, AccSmem& A, int tid, int lane)
+{
+    Dens d;
+    d.load(M);
+    run_item<PREC, Dens>(M, d, node, chunk, out, A, tid, lane);
+}
+
+// ------------------------------------------------------ path kernel ----
+// Mesh record of work item `item` (batched launches: binary search of the
+// per-mesh item offsets; single-mesh launches: the record passed by value and
+// staged in shared memory by the block).
+__device__ __forceinline__ int find_mesh(const uint64_t* __restrict__ off, int n_meshes, uint64_t x)
+{
+    int lo = 0, hi = n_meshes;                 // off[lo] <= x < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(MC_THREADS, PREC == SDD_FP64 ? SDD_MC_MIN_BLOCKS_F64 : SDD_MC_MIN_BLOCKS_F32)
+k_paths(McArgs a)
+{
+    __shared__ AccSmem acc;
+    __shared__ MeshDev single;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    if (a.meshes == nullptr) {
+        const int* src = reinterpret_cast<const int*>(&a.single);
+        int* dst = reinterpret_cast<int*>(&single);
+        for (int q = tid; q < (int)(sizeof(MeshDev) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+        __syncthreads();
+    }
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.queue, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= a.total_items) return;
+        int m = 0;
+        if (a.meshes != nullptr) m = find_mesh(a.item_off, a.n_meshes, item);
+        const MeshDev& M = a.meshes != nullptr ? a.meshes[m] : single;
+        const uint64_t local = item - M.item_begin;
+        const uint32_t node = (uint32_t)(local / M.chunks_per_node);
+        const uint32_t chunk = (uint32_t)(local % M.chunks_per_node);
+        Slot* out = a.slots + item;
+        if constexpr (PREC == SDD_FP64) {
+            switch (M.family) {
+                case SDD_FAMILY_RING: run_with<PREC, RingF64>(M, node, chunk, out, acc, tid, lane); break;
+                case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF64>(M, node, chunk, out, acc, tid, lane); break;
+                default: run_with<PREC, BumpsF64>(M, node, chunk, out, acc, tid, lane); break;
+            }
+        } else {
+            switch (M.family) {
+                case SDD_FAMILY_RING: run_with<PREC, RingF32>(M, node, chunk, out, acc, tid, lane); break;
+                case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF32>(M, node, chunk, out, acc, tid, lane); break;
+                default:
+                    if (M.nb <= 1) run_with<PREC, BumpsF32<1>>(M, node, chunk, out, acc, tid, lane);
+                    else if (M.nb == 2) run_with<PREC, BumpsF32<2>>(M, node, chunk, out, acc, tid, lane);
+                    else if (M.nb == 3) run_with<PREC, BumpsF32<3>>(M, node, chunk, out, acc, tid, lane);
+                    else run_with<PREC, BumpsF32<SDD_MAX_BUMPS>>(M, node, chunk, out, acc, tid, lane);
+                    break;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------- per-node reduction ----
+// One thread per node: the node's chunk slots are combined in chunk order
+// (compensated), then mean = X0 + S/N and stderr = sqrt((Q - S^2/N)/(N(N-1)))
+// (§2.2), and the mesh's counters are accumulated (integer atomics and an
+// atomic max of the non-negative stderr bit pattern: order-independent).
+__global__ void __launch_bounds__(256) k_reduce(McArgs a)
+{
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.total_nodes) return;
+    int m = 0;
+    if (a.meshes != nullptr) m = find_mesh(a.node_off, a.n_meshes, g);
+    const MeshDev& M = a.meshes != nullptr ? a.meshes[m] : a.single;
+    const uint64_t v = g - M.node_begin;
+    const uint64_t base = M.item_begin + v * M.chunks_per_node;
+    double sh[2] = {0, 0}, sl[2] = {0, 0}, qh[2] = {0, 0}, ql[2] = {0, 0};
+    double st[2] = {0, 0}, qt[2] = {0, 0};
+    unsigned long long ties = 0, caps = 0, steps = 0;
+    for (uint32_t c = 0; c < M.chunks_per_node; ++c) {
+        const Slot& S = a.slots[base + c];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            sl[q] += S.s_lo[q];
+            two_sum_add(sh[q], sl[q], S.s_hi[q]);
+            ql[q] += S.q_lo[q];
+            two_sum_add(qh[q], ql[q], S.q_hi[q]);
+            st[q] += S.st[q];
+            qt[q] += S.qt[q];
+        }
+        ties += S.ties;
+        caps += S.caps;
+        steps += S.steps;
+    }
+    const double N = (double)M.paths;
+    const int2 ij = M.nodes[v];
+    const double x0[2] = {(double)ij.x / (double)(M.n - 1), (double)ij.y / (double)(M.n - 1)};
+    sdd_node_sums out;
+    double se_max = 0.0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const double snt = sh[q] + sl[q];
+        const double qnt = qh[q] + ql[q];
+        out.sum_nt[q] = snt;
+        out.sumsq_nt[q] = qnt;
+        out.sum[q] = snt + st[q];
+        out.sumsq[q] = qnt + qt[q];
+        const double S = out.sum[q], Q = out.sumsq[q];
+        const double var = fmax(Q - S * S / N, 0.0) / (N * (N - 1.0));
+        const double se = sqrt(var);
+        se_max = fmax(se_max, se);
+        if (M.mean) M.mean[2 * v + q] = x0[q] + S / N;
+        if (M.stderr_) M.stderr_[2 * v + q] = se;
+    }
+    out.paths = M.paths;
+    out.ties = ties;
+    out.non_exits = caps;
+    out.steps = steps;
+    if (M.sums) M.sums[v] = out;
+    atomicAdd(&M.stats->steps, steps);
+    atomicAdd(&M.stats->ties, ties);
+    atomicAdd(&M.stats->caps, caps);
+    atomicMax(&M.stats->max_stderr_bits, (unsigned long long)__double_as_longlong(se_max));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side ----
+void fill_fp32_params(MeshDev& m, const sdd_density& d)
+{
+    const double LOG2E = 1.44269504088896340736;
+    for (int q = 0; q < 48; ++q) m.pf[q] = 0.0f;
+    for (int q = 0; q < 32; ++q) m.pd[q] = q < d.n_params ? d.params[q] : 0.0;
+    m.sgn = d.coef_mode == SDD_COEF_INV_W ? -1.0 : 1.0;
+    if (d.family == SDD_FAMILY_BUMPS) {
+        const int nb = (int)d.params[0];
+        m.nb = nb;
+        for (int b = 0; b < nb; ++b) {
+            const double* q = d.params + 1 + 5 * b;
+            m.pf[8 * b + 0] = (float)q[0];
+            m.pf[8 * b + 1] = (float)q[1];
+            m.pf[8 * b + 2] = (float)q[2];
+            m.pf[8 * b + 3] = (float)(q[3] * LOG2E);
+            m.pf[8 * b + 4] = (float)(q[4] * LOG2E);
+            m.pf[8 * b + 5] = (float)(-2.0 * q[3]);
+            m.pf[8 * b + 6] = (float)(-2.0 * q[4]);
+        }
+    } else if (d.family == SDD_FAMILY_RING) {
+        const double A = d.params[0], cs = d.params[1], ct = d.params[2], k = d.params[3],
+                     r0 = d.params[4];
+        m.nb = 0;
+        m.pf[0] = (float)cs;
+        m.pf[1] = (float)ct;
+        m.pf[2] = (float)r0;
+        m.pf[3] = (float)(-2.0 * k * LOG2E);
+        m.pf[4] = (float)(4.0 * A);
+        m.pf[5] = (float)(m.sgn * -8.0 * A * k);
+        // u = k (r - r0): the kernel forms r - r0 and folds k into c1 and K
+    } else {
+        const double A = d.params[0], k = d.params[1], t0 = d.params[2], a = d.params[3],
+                     f = d.params[4];
+        m.nb = 0;
+        m.pf[0] = (float)A;
+        m.pf[1] = (float)(k * LOG2E);
+        m.pf[2] = (float)t0;
+        m.pf[3] = (float)a;
+        m.pf[4] = (float)f;
+        m.pf[5] = (float)(-2.0 * k);
+        m.pf[6] = (float)(-2.0 * 3.14159265358979323846 * a * f);
+    }
+}
+
+int mc_grid_blocks(int precision, int* blocks, int* threads)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    SDD_CUDA(cudaGetDevice(&dev));
+    SDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (precision == SDD_FP64)
+        SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<SDD_FP64>,
+                                                                MC_THREADS, 0));
+    else
+        SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<SDD_FP32_STEP>,
+                                                                MC_THREADS, 0));
+    *blocks = sms * std::max(per_sm, 1);
+    *threads = MC_THREADS;
+    return SDD_OK;
+}
+
+int launch_mc(const McArgs& args, int precision, cudaStream_t stream)
+{
+    if (args.total_items == 0) return SDD_OK;
+    int blocks = 0, threads = 0;
+    int rc = mc_grid_blocks(precision, &blocks, &threads);
+    if (rc) return rc;
+    const uint64_t max_blocks = (args.total_items * 32 + threads - 1) / threads;
+    if ((uint64_t)blocks > max_blocks) blocks = (int)max_blocks;
+    SDD_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
+    if (precision == SDD_FP64)
+        k_paths<SDD_FP64><<<blocks, threads, 0, stream>>>(args);
+    else
+        k_paths<SDD_FP32_STEP><<<blocks, threads, 0, stream>>>(args);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    const unsigned rb = (unsigned)((args.total_nodes + 255) / 256);
+    k_reduce<<<rb, 256, 0, stream>>>(args);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
+
+}  // namespace sdd

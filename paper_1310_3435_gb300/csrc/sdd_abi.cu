@@ -1,0 +1,702 @@
+// C ABI of libsdd.so: plans, interface Monte Carlo, subdomain solves and the
+// combined mesh generation (Bihlo & Haynes, §2.1-2.2, §3.2, §3.5).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sdd_internal.h"
+
+// ------------------------------------------------------------------ plan --
+struct sdd_plan {
+    int n = 0, sx = 0, sy = 0;
+    int device = 0;
+    sdd_density dens{};
+    int bmap_mode = 0;
+    std::vector<int> ix, iy;               // interface lines
+    std::vector<int32_t> h_nodes;          // [n_nodes][2] (i, j)
+    std::vector<double> h_edges;           // [2][4][n]
+    std::vector<sdd::SubDev> h_subs;
+    int64_t n_nodes = 0;
+
+    int2* d_nodes = nullptr;
+    double* d_edges = nullptr;
+
+    // Monte Carlo
+    unsigned long long* d_queue = nullptr;
+    sdd::Slot* d_slots = nullptr;
+    uint64_t slots_cap = 0;
+    sdd_node_sums* d_sums = nullptr;
+    double* d_mean = nullptr;
+    double* d_stderr = nullptr;
+    sdd::McStatsDev* d_stats = nullptr;
+    uint64_t last_paths = 0;
+    bool have_mc = false;
+
+    // subdomain solves
+    double* d_u = nullptr;
+    double* d_cx = nullptr;
+    double* d_cy = nullptr;
+    float* d_cxf = nullptr;
+    float* d_cyf = nullptr;
+    float* d_work = nullptr;
+    sdd::SubDev* d_subs = nullptr;
+    sdd::SubStat* d_substats = nullptr;
+    bool coefs_ready = false;
+
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace sdd {
+
+// ---------------------------------------------------------------- errors --
+namespace {
+thread_local std::string g_error;
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void set_error(const std::string& msg) { g_error = msg; }
+void clear_error() { g_error.clear(); }
+int fail(int code, const std::string& msg)
+{
+    g_error = msg;
+    return code;
+}
+int cuda_status(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return SDD_OK;
+    g_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return SDD_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return SDD_ERR_NO_DEVICE;
+    return SDD_ERR_CUDA;
+}
+void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+
+// Device (or managed) memory?  Anything else is host memory and is copied.
+bool is_device_ptr(const void* p)
+{
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    SDD_CUDA(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+    return SDD_OK;
+}
+
+template <typename T>
+void dev_free(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Interface lines of an s-way split of n points: I_k = round(k (n-1)/s),
+// halves rounded up, exact integer arithmetic.
+std::vector<int> interface_lines(int n, int s)
+{
+    std::vector<int> v;
+    for (int k = 1; k < s; ++k) v.push_back((int)((2LL * k * (n - 1) + s) / (2LL * s)));
+    return v;
+}
+
+// Host FP64 evaluation of c for the paper's 1D boundary forms (§3.2).
+double host_coef(const sdd_density& d, double s, double t)
+{
+    const double* p = d.params;
+    double w;
+    if (d.family == SDD_FAMILY_RING) {
+        const double ds = s - p[1], dtt = t - p[2];
+        const double u = p[3] * (std::sqrt(ds * ds + dtt * dtt) - p[4]);
+        const double e = std::exp(-2.0 * std::fabs(u));
+        w = 1.0 + p[0] * 4.0 * e / ((1.0 + e) * (1.0 + e));
+    } else if (d.family == SDD_FAMILY_RIDGE) {
+        const double v = t - p[2] - p[3] * std::sin(2.0 * 3.14159265358979323846 * p[4] * s);
+        w = 1.0 + p[0] * std::exp(-p[1] * v * v);
+    } else {
+        w = 1.0;
+        const int nb = (int)p[0];
+        for (int b = 0; b < nb; ++b) {
+            const double* q = p + 1 + 5 * b;
+            const double ds = s - q[1], dtt = t - q[2];
+            w += q[0] * std::exp(-(q[3] * ds * ds + q[4] * dtt * dtt));
+        }
+    }
+    return d.coef_mode == SDD_COEF_INV_W ? 1.0 / w : w;
+}
+
+int validate_density(const sdd_density* d)
+{
+    if (!d) return fail(SDD_ERR_INVALID_ARG, "density is NULL");
+    if (d->coef_mode != SDD_COEF_W && d->coef_mode != SDD_COEF_INV_W)
+        return fail(SDD_ERR_INVALID_ARG, "unknown coef_mode");
+    if (d->n_params < 0 || d->n_params > SDD_MAX_PARAMS)
+        return fail(SDD_ERR_INVALID_ARG, "n_params out of range");
+    for (int q = 0; q < d->n_params; ++q)
+        if (!std::isfinite(d->params[q])) return fail(SDD_ERR_INVALID_ARG, "non-finite parameter");
+    if (d->family == SDD_FAMILY_BUMPS) {
+        if (d->n_params < 1) return fail(SDD_ERR_INVALID_ARG, "BUMPS needs params[0] = nb");
+        const double nbd = d->params[0];
+        const int nb = (int)nbd;
+        if (nbd != (double)nb || nb < 0 || nb > SDD_MAX_BUMPS)
+            return fail(SDD_ERR_INVALID_ARG, "BUMPS: nb must be an integer in 0..6");
+        if (d->n_params < 1 + 5 * nb) return fail(SDD_ERR_INVALID_ARG, "BUMPS: too few params");
+        for (int b = 0; b < nb; ++b) {
+            const double* q = d->params + 1 + 5 * b;
+            if (q[3] < 0 || q[4] < 0) return fail(SDD_ERR_INVALID_ARG, "BUMPS: ks, kt must be >= 0");
+            if (q[0] <= -1.0 / nb) return fail(SDD_ERR_INVALID_ARG, "BUMPS: w must stay positive");
+        }
+    } else if (d->family == SDD_FAMILY_RING || d->family == SDD_FAMILY_RIDGE) {
+        if (d->n_params < 5) return fail(SDD_ERR_INVALID_ARG, "RING/RIDGE need 5 params");
+        if (d->params[0] <= -1.0) return fail(SDD_ERR_INVALID_ARG, "w must stay positive");
+        if (d->family == SDD_FAMILY_RIDGE && d->params[1] < 0)
+            return fail(SDD_ERR_INVALID_ARG, "RIDGE: k must be >= 0");
+    } else {
+        return fail(SDD_ERR_INVALID_ARG, "unknown density family");
+    }
+    return SDD_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_device(const sdd_plan* p)
+{
+    int dev = -1;
+    SDD_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device)
+        return fail(SDD_ERR_INVALID_ARG, "plan belongs to another device than the current one");
+    return SDD_OK;
+}
+
+int ensure_mc_buffers(sdd_plan* p, uint64_t items)
+{
+    if (!p->d_sums) {
+        int rc;
+        if ((rc = dev_alloc(&p->d_sums, (size_t)p->n_nodes))) return rc;
+        if ((rc = dev_alloc(&p->d_mean, (size_t)p->n_nodes * 2))) return rc;
+        if ((rc = dev_alloc(&p->d_stderr, (size_t)p->n_nodes * 2))) return rc;
+        if ((rc = dev_alloc(&p->d_stats, 1))) return rc;
+        if ((rc = dev_alloc(&p->d_queue, 1))) return rc;
+    }
+    if (items > p->slots_cap) {
+        dev_free(p->d_slots);
+        p->slots_cap = 0;
+        int rc = dev_alloc(&p->d_slots, (size_t)items);
+        if (rc) return rc;
+        p->slots_cap = items;
+    }
+    return SDD_OK;
+}
+
+int ensure_solve_buffers(sdd_plan* p, cudaStream_t stream)
+{
+    const int64_t nn = (int64_t)p->n * p->n;
+    if (!p->d_u) {
+        int rc;
+        if ((rc = dev_alloc(&p->d_u, (size_t)nn * 2))) return rc;
+        if ((rc = dev_alloc(&p->d_cx, (size_t)p->n * (p->n - 1)))) return rc;
+        if ((rc = dev_alloc(&p->d_cy, (size_t)p->n * (p->n - 1)))) return rc;
+        if ((rc = dev_alloc(&p->d_cxf, (size_t)p->n * (p->n - 1)))) return rc;
+        if ((rc = dev_alloc(&p->d_cyf, (size_t)p->n * (p->n - 1)))) return rc;
+        if ((rc = dev_alloc(&p->d_work, (size_t)nn * 9))) return rc;
+        if ((rc = dev_alloc(&p->d_subs, p->h_subs.size()))) return rc;
+        if ((rc = dev_alloc(&p->d_substats, p->h_subs.size()))) return rc;
+        SDD_CUDA(cudaMemcpy(p->d_subs, p->h_subs.data(), p->h_subs.size() * sizeof(SubDev),
+                            cudaMemcpyHostToDevice));
+        SDD_CUDA(cudaMemsetAsync(p->d_work, 0, (size_t)nn * 9 * sizeof(float), stream));
+    }
+    if (!p->coefs_ready) {
+        int rc = launch_edge_coefs(p->n, p->dens.family, p->dens.coef_mode, p->dens.params,
+                                   p->d_cx, p->d_cy, p->d_cxf, p->d_cyf, stream);
+        if (rc) return rc;
+        p->coefs_ready = true;
+    }
+    return SDD_OK;
+}
+
+// Paths per work item: enough items to spread over every warp slot of the
+// device several times, at least 64 and at most 4096 paths per item.  It
+// depends only on the mesh's own node count and N, so a mesh's sums are the
+// same alone and inside a batch.
+uint32_t auto_chunk(uint64_t paths, int64_t n_nodes)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    (void)dev;
+    const double target = (double)paths * (double)n_nodes / (32.0 * 24.0 * (double)sms);
+    uint32_t c = 64;
+    while (c < 4096 && (double)(2 * c) <= target) c *= 2;
+    const uint32_t cap = (uint32_t)(((paths + 31) / 32) * 32);
+    return std::min(c, cap);
+}
+
+int validate_mc(const sdd_mc_params* mc)
+{
+    if (!mc) return fail(SDD_ERR_INVALID_ARG, "mc params are NULL");
+    if (mc->paths_per_node < 2 || mc->paths_per_node >= (1ull << 32))
+        return fail(SDD_ERR_INVALID_ARG, "paths_per_node must be in [2, 2^32)");
+    if (!(mc->dt > 0.0) || !std::isfinite(mc->dt))
+        return fail(SDD_ERR_INVALID_ARG, "dt must be positive and finite");
+    if (mc->precision != SDD_FP64 && mc->precision != SDD_FP32_STEP)
+        return fail(SDD_ERR_INVALID_ARG, "unknown precision");
+    if (mc->chunk < 0 || (mc->chunk > 0 && mc->chunk % 32 != 0))
+        return fail(SDD_ERR_INVALID_ARG, "chunk must be 0 or a positive multiple of 32");
+    const double cap = mc->max_steps ? (double)mc->max_steps : std::ceil(2.0 / mc->dt);
+    if (cap < 1.0 || cap > 4294967294.0)
+        return fail(SDD_ERR_INVALID_ARG, "max_steps must be in [1, 2^32 - 2]");
+    return SDD_OK;
+}
+
+// Builds the mesh record and launches the path kernel + reduction.
+int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stderr_dev,
+           sdd_node_sums* sums_dev, cudaStream_t stream)
+{
+    int rc = validate_mc(mc);
+    if (rc) return rc;
+    const uint32_t chunk = mc->chunk ? (uint32_t)mc->chunk : auto_chunk(mc->paths_per_node, p->n_nodes);
+    const uint32_t cpn = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
+    const uint64_t items = (uint64_t)p->n_nodes * cpn;
+    if ((rc = ensure_mc_buffers(p, items))) return rc;
+
+    McArgs a;
+    memset(&a, 0, sizeof(a));
+    MeshDev& m = a.single;
+    m.n = p->n;
+    m.family = p->dens.family;
+    m.precision = mc->precision;
+    m.key0 = (uint32_t)(mc->seed & 0xffffffffu);
+    m.key1 = (uint32_t)(mc->seed >> 32);
+    m.paths = (uint32_t)mc->paths_per_node;
+    m.chunk = chunk;
+    m.chunks_per_node = cpn;
+    m.max_steps = (uint32_t)(mc->max_steps ? mc->max_steps : (uint64_t)std::ceil(2.0 / mc->dt));
+    m.n_nodes = p->n_nodes;
+    m.item_begin = 0;
+    m.node_begin = 0;
+    m.dt = mc->dt;
+    m.sqrt2dt = std::sqrt(2.0 * mc->dt);
+    m.tie_delta = mc->tie_delta >= 0.0 ? mc->tie_delta : (mc->precision == SDD_FP64 ? 1e-11 : 0.0);
+    m.nodes = p->d_nodes;
+    m.edges = p->d_edges;
+    m.sums = sums_dev ? sums_dev : p->d_sums;
+    m.mean = mean_dev ? mean_dev : p->d_mean;
+    m.stderr_ = stderr_dev ? stderr_dev : p->d_stderr;
+    m.stats = p->d_stats;
+    fill_fp32_params(m, p->dens);
+    a.meshes = nullptr;
+    a.n_meshes = 1;
+    a.total_items = items;
+    a.total_nodes = (uint64_t)p->n_nodes;
+    a.queue = p->d_queue;
+    a.slots = p->d_slots;
+    SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
+    if ((rc = launch_mc(a, mc->precision, stream))) return rc;
+    p->last_paths = mc->paths_per_node;
+    p->have_mc = true;
+    p->last_stream = stream;
+    return SDD_OK;
+}
+
+int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
+{
+    McStatsDev s;
+    SDD_CUDA(cudaMemcpyAsync(&s, p->d_stats, sizeof(s), cudaMemcpyDeviceToHost, stream));
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    out->paths = p->last_paths * (uint64_t)p->n_nodes;
+    out->path_steps = s.steps;
+    out->ties = s.ties;
+    out->non_exits = s.caps;
+    double se;
+    memcpy(&se, &s.max_stderr_bits, sizeof(se));
+    out->max_stderr = se;
+    return SDD_OK;
+}
+
+int validate_solve(const sdd_solve_params* sp)
+{
+    if (!sp) return fail(SDD_ERR_INVALID_ARG, "solve params are NULL");
+    if (sp->solver != SDD_SOLVER_SOR && sp->solver != SDD_SOLVER_CG_FP32_REFINE)
+        return fail(SDD_ERR_INVALID_ARG, "unknown solver");
+    if (!(sp->tol > 0.0) || !std::isfinite(sp->tol))
+        return fail(SDD_ERR_INVALID_ARG, "tol must be positive");
+    if (sp->max_iter < 0) return fail(SDD_ERR_INVALID_ARG, "max_iter must be >= 0");
+    if (!(sp->omega == 0.0 || (sp->omega > 0.0 && sp->omega < 2.0)))
+        return fail(SDD_ERR_INVALID_ARG, "omega must be 0 or in (0, 2)");
+    return SDD_OK;
+}
+
+// Fills the mesh from the boundary tables and device interface values, then
+// solves every subdomain.  Result in p->d_u.
+int run_solve(sdd_plan* p, const double* iface_dev, const sdd_solve_params* sp,
+              cudaStream_t stream)
+{
+    int rc = validate_solve(sp);
+    if (rc) return rc;
+    if ((rc = ensure_solve_buffers(p, stream))) return rc;
+    SolveMeshDev sm;
+    memset(&sm, 0, sizeof(sm));
+    sm.n = p->n;
+    sm.solver = sp->solver;
+    sm.max_iter = sp->max_iter > 0 ? sp->max_iter : (sp->solver == SDD_SOLVER_SOR ? 200000 : 20000);
+    sm.tol = sp->tol;
+    sm.omega = sp->omega;
+    sm.u = p->d_u;
+    sm.cx = p->d_cx;
+    sm.cy = p->d_cy;
+    sm.cxf = p->d_cxf;
+    sm.cyf = p->d_cyf;
+    sm.work = p->d_work;
+    if ((rc = launch_fill_mesh(p->n, p->d_edges, p->d_nodes, p->n_nodes, iface_dev, p->d_u,
+                               p->d_subs, (int)p->h_subs.size(), stream)))
+        return rc;
+    SolveArgs a;
+    a.meshes = nullptr;
+    a.single = sm;
+    a.subs = p->d_subs;
+    a.n_subs = (int)p->h_subs.size();
+    a.stats = p->d_substats;
+    if ((rc = launch_solve(a, stream))) return rc;
+    p->last_stream = stream;
+    return SDD_OK;
+}
+
+int read_solve_stats(sdd_plan* p, sdd_solve_stats* out, cudaStream_t stream)
+{
+    std::vector<SubStat> st(p->h_subs.size());
+    if (!st.empty())
+        SDD_CUDA(cudaMemcpyAsync(st.data(), p->d_substats, st.size() * sizeof(SubStat),
+                                 cudaMemcpyDeviceToHost, stream));
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    out->subdomains = (int32_t)st.size();
+    out->converged = 0;
+    out->max_iterations = 0;
+    out->max_rel_residual = 0.0;
+    for (const SubStat& s : st) {
+        out->converged += s.converged;
+        out->max_iterations = std::max(out->max_iterations, s.iterations);
+        out->max_rel_residual = std::max(out->max_rel_residual, s.rel_residual);
+    }
+    return out->converged == out->subdomains
+               ? SDD_OK
+               : fail(SDD_ERR_NOT_CONVERGED, "a subdomain did not reach the tolerance");
+}
+
+}  // namespace
+}  // namespace sdd
+
+using namespace sdd;
+
+extern "C" {
+
+int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap* bmap,
+                  sdd_plan** out)
+{
+    clear_error();
+    if (!out) return fail(SDD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 3 || n > 16385) return fail(SDD_ERR_INVALID_ARG, "n must be in [3, 16385]");
+    if (sx < 1 || sy < 1 || sx > n - 1 || sy > n - 1)
+        return fail(SDD_ERR_INVALID_ARG, "sx, sy must be in [1, n-1]");
+    int rc = validate_density(dens);
+    if (rc) return rc;
+    if (!bmap) return fail(SDD_ERR_INVALID_ARG, "bmap is NULL");
+    if (bmap->mode != SDD_BMAP_IDENTITY && bmap->mode != SDD_BMAP_PAPER_1D &&
+        bmap->mode != SDD_BMAP_TABLE)
+        return fail(SDD_ERR_INVALID_ARG, "unknown boundary-map mode");
+    if (bmap->mode == SDD_BMAP_TABLE && !bmap->edges)
+        return fail(SDD_ERR_INVALID_ARG, "TABLE boundary map needs edges");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SDD_ERR_NO_DEVICE, "no CUDA device");
+    }
+    sdd_plan* p = new (std::nothrow) sdd_plan();
+    if (!p) return fail(SDD_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&p->device);
+    p->n = n;
+    p->sx = sx;
+    p->sy = sy;
+    p->dens = *dens;
+    for (int q = dens->n_params; q < SDD_MAX_PARAMS; ++q) p->dens.params[q] = 0.0;
+    p->bmap_mode = bmap->mode;
+    p->ix = interface_lines(n, sx);
+    p->iy = interface_lines(n, sy);
+
+    // interface nodes, ordered by j then i
+    std::vector<char> onx(n, 0), ony(n, 0);
+    for (int v : p->ix) onx[v] = 1;
+    for (int v : p->iy) ony[v] = 1;
+    for (int j = 1; j < n - 1; ++j)
+        for (int i = 1; i < n - 1; ++i)
+            if (onx[i] || ony[j]) {
+                p->h_nodes.push_back(i);
+                p->h_nodes.push_back(j);
+            }
+    p->n_nodes = (int64_t)p->h_nodes.size() / 2;
+
+    // subdomain boxes
+    std::vector<int> X{0}, Y{0};
+    X.insert(X.end(), p->ix.begin(), p->ix.end());
+    X.push_back(n - 1);
+    Y.insert(Y.end(), p->iy.begin(), p->iy.end());
+    Y.push_back(n - 1);
+    for (int b = 0; b < sy; ++b)
+        for (int a = 0; a < sx; ++a) p->h_subs.push_back(SubDev{0, X[a], X[a + 1], Y[b], Y[b + 1]});
+
+    // boundary tables [2][4][n]
+    p->h_edges.assign((size_t)8 * n, 0.0);
+    auto E = [&](int c, int edge, int k) -> double& { return p->h_edges[((size_t)c * 4 + edge) * n + k]; };
+    if (bmap->mode == SDD_BMAP_TABLE) {
+        for (size_t q = 0; q < p->h_edges.size(); ++q) {
+            if (!std::isfinite(bmap->edges[q])) {
+                delete p;
+                return fail(SDD_ERR_INVALID_ARG, "non-finite boundary table value");
+            }
+            p->h_edges[q] = bmap->edges[q];
+        }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            const double x = (double)k / (double)(n - 1);
+            E(0, 0, k) = x; E(0, 1, k) = x; E(0, 2, k) = 0.0; E(0, 3, k) = 1.0;
+            E(1, 0, k) = 0.0; E(1, 1, k) = 1.0; E(1, 2, k) = x; E(1, 3, k) = x;
+        }
+        if (bmap->mode == SDD_BMAP_PAPER_1D) {
+            // u_k = sum_{m<k} 1/c_{m+1/2} / sum_m 1/c_{m+1/2} along each edge
+            for (int edge = 0; edge < 4; ++edge) {
+                const int comp = edge < 2 ? 0 : 1;
+                std::vector<double> cum(n, 0.0);
+                for (int m = 0; m < n - 1; ++m) {
+                    const double mid = ((double)m + 0.5) / (double)(n - 1);
+                    double s, t;
+                    if (edge == 0) { s = mid; t = 0.0; }
+                    else if (edge == 1) { s = mid; t = 1.0; }
+                    else if (edge == 2) { s = 0.0; t = mid; }
+                    else { s = 1.0; t = mid; }
+                    cum[m + 1] = cum[m] + 1.0 / host_coef(p->dens, s, t);
+                }
+                for (int k = 0; k < n; ++k) E(comp, edge, k) = cum[k] / cum[n - 1];
+            }
+        }
+    }
+
+    if ((rc = dev_alloc(&p->d_nodes, (size_t)std::max<int64_t>(p->n_nodes, 1))) ||
+        (rc = dev_alloc(&p->d_edges, p->h_edges.size()))) {
+        sdd_plan_destroy(p);
+        return rc;
+    }
+    cudaError_t ce = cudaSuccess;
+    if (p->n_nodes > 0)
+        ce = cudaMemcpy(p->d_nodes, p->h_nodes.data(), p->h_nodes.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(p->d_edges, p->h_edges.data(), p->h_edges.size() * sizeof(double),
+                        cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        rc = cuda_status(ce, "cudaMemcpy(plan tables)");
+        sdd_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return SDD_OK;
+}
+
+int sdd_plan_num_nodes(const sdd_plan* plan, int64_t* n_nodes)
+{
+    clear_error();
+    if (!plan || !n_nodes) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    *n_nodes = plan->n_nodes;
+    return SDD_OK;
+}
+
+int sdd_plan_nodes(const sdd_plan* plan, int32_t* ij)
+{
+    clear_error();
+    if (!plan || !ij) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    std::copy(plan->h_nodes.begin(), plan->h_nodes.end(), ij);
+    return SDD_OK;
+}
+
+int sdd_plan_edges(const sdd_plan* plan, double* edges)
+{
+    clear_error();
+    if (!plan || !edges) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    std::copy(plan->h_edges.begin(), plan->h_edges.end(), edges);
+    return SDD_OK;
+}
+
+int sdd_interface_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean, double* stderr_,
+                     sdd_mc_stats* stats, void* stream_)
+{
+    clear_error();
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_device(p);
+    if (rc) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    const bool mean_dev = is_device_ptr(mean), se_dev = is_device_ptr(stderr_);
+    if ((rc = run_mc(p, mc, mean_dev ? mean : nullptr, se_dev ? stderr_ : nullptr, nullptr, stream)))
+        return rc;
+    const size_t bytes = (size_t)p->n_nodes * 2 * sizeof(double);
+    bool host = false;
+    if (mean && !mean_dev && bytes) {
+        SDD_CUDA(cudaMemcpyAsync(mean, p->d_mean, bytes, cudaMemcpyDeviceToHost, stream));
+        host = true;
+    }
+    if (stderr_ && !se_dev && bytes) {
+        SDD_CUDA(cudaMemcpyAsync(stderr_, p->d_stderr, bytes, cudaMemcpyDeviceToHost, stream));
+        host = true;
+    }
+    if (stats) return read_mc_stats(p, stats, stream);
+    if (host) SDD_CUDA(cudaStreamSynchronize(stream));
+    return SDD_OK;
+}
+
+int sdd_interface_mc_sums(sdd_plan* p, const sdd_mc_params* mc, sdd_node_sums* sums,
+                          void* stream_)
+{
+    clear_error();
+    if (!p || !sums) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_device(p);
+    if (rc) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    const bool dev = is_device_ptr(sums);
+    if ((rc = run_mc(p, mc, nullptr, nullptr, dev ? sums : nullptr, stream))) return rc;
+    if (!dev && p->n_nodes > 0) {
+        SDD_CUDA(cudaMemcpyAsync(sums, p->d_sums, (size_t)p->n_nodes * sizeof(sdd_node_sums),
+                                 cudaMemcpyDeviceToHost, stream));
+        SDD_CUDA(cudaStreamSynchronize(stream));
+    }
+    return SDD_OK;
+}
+
+int sdd_plan_last_mc_stats(sdd_plan* p, sdd_mc_stats* stats)
+{
+    clear_error();
+    if (!p || !stats) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (!p->have_mc) return fail(SDD_ERR_INVALID_ARG, "no Monte Carlo call on this plan yet");
+    int rc = check_device(p);
+    if (rc) return rc;
+    return read_mc_stats(p, stats, p->last_stream);
+}
+
+int sdd_subdomain_solve(sdd_plan* p, const double* iface, const sdd_solve_params* sp, double* mesh,
+                        sdd_solve_stats* stats, void* stream_)
+{
+    clear_error();
+    if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (!iface && p->n_nodes > 0) return fail(SDD_ERR_INVALID_ARG, "iface is NULL");
+    int rc = check_device(p);
+    if (rc) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    const size_t ibytes = (size_t)p->n_nodes * 2 * sizeof(double);
+    const double* iface_dev = iface;
+    if (iface && !is_device_ptr(iface)) {
+        if ((rc = ensure_mc_buffers(p, 0))) return rc;
+        SDD_CUDA(cudaMemcpyAsync(p->d_mean, iface, ibytes, cudaMemcpyHostToDevice, stream));
+        iface_dev = p->d_mean;
+    }
+    if ((rc = run_solve(p, iface_dev, sp, stream))) return rc;
+    const size_t mbytes = (size_t)p->n * p->n * 2 * sizeof(double);
+    if (is_device_ptr(mesh)) {
+        SDD_CUDA(cudaMemcpyAsync(mesh, p->d_u, mbytes, cudaMemcpyDeviceToDevice, stream));
+    } else {
+        SDD_CUDA(cudaMemcpyAsync(mesh, p->d_u, mbytes, cudaMemcpyDeviceToHost, stream));
+        SDD_CUDA(cudaStreamSynchronize(stream));
+    }
+    if (stats) return read_solve_stats(p, stats, stream);
+    return SDD_OK;
+}
+
+int sdd_mesh_generate(sdd_plan* p, const sdd_mc_params* mc, const sdd_solve_params* sp,
+                      double* mesh, double* iface_mean, double* iface_stderr,
+                      sdd_mc_stats* mc_stats, sdd_solve_stats* solve_stats, void* stream_)
+{
+    clear_error();
+    if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = validate_solve(sp))) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    if ((rc = run_mc(p, mc, nullptr, nullptr, nullptr, stream))) return rc;
+    if ((rc = run_solve(p, p->d_mean, sp, stream))) return rc;
+    const size_t mbytes = (size_t)p->n * p->n * 2 * sizeof(double);
+    const size_t ibytes = (size_t)p->n_nodes * 2 * sizeof(double);
+    bool host = false;
+    if (is_device_ptr(mesh)) {
+        SDD_CUDA(cudaMemcpyAsync(mesh, p->d_u, mbytes, cudaMemcpyDeviceToDevice, stream));
+    } else {
+        SDD_CUDA(cudaMemcpyAsync(mesh, p->d_u, mbytes, cudaMemcpyDeviceToHost, stream));
+        host = true;
+    }
+    if (iface_mean && ibytes) {
+        const bool d = is_device_ptr(iface_mean);
+        SDD_CUDA(cudaMemcpyAsync(iface_mean, p->d_mean, ibytes,
+                                 d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        host = host || !d;
+    }
+    if (iface_stderr && ibytes) {
+        const bool d = is_device_ptr(iface_stderr);
+        SDD_CUDA(cudaMemcpyAsync(iface_stderr, p->d_stderr, ibytes,
+                                 d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        host = host || !d;
+    }
+    if (mc_stats && (rc = read_mc_stats(p, mc_stats, stream))) return rc;
+    if (solve_stats) return read_solve_stats(p, solve_stats, stream);
+    if (host) SDD_CUDA(cudaStreamSynchronize(stream));
+    return SDD_OK;
+}
+
+void sdd_plan_destroy(sdd_plan* p)
+{
+    if (!p) return;
+    if (p->last_stream || p->have_mc) cudaStreamSynchronize(p->last_stream);
+    dev_free(p->d_nodes);
+    dev_free(p->d_edges);
+    dev_free(p->d_queue);
+    dev_free(p->d_slots);
+    dev_free(p->d_sums);
+    dev_free(p->d_mean);
+    dev_free(p->d_stderr);
+    dev_free(p->d_stats);
+    dev_free(p->d_u);
+    dev_free(p->d_cx);
+    dev_free(p->d_cy);
+    dev_free(p->d_cxf);
+    dev_free(p->d_cyf);
+    dev_free(p->d_work);
+    dev_free(p->d_subs);
+    dev_free(p->d_substats);
+    delete p;
+}
+
+const char* sdd_last_error(void) { return g_error.c_str(); }
+
+int sdd_kernel_launches(uint64_t* count)
+{
+    if (!count) return fail(SDD_ERR_INVALID_ARG, "count is NULL");
+    *count = g_launches.load(std::memory_order_relaxed);
+    return SDD_OK;
+}
+
+}  // extern "C"

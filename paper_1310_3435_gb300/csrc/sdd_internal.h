@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of libsdd.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sdd.h"
+
+namespace sdd {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const std::string& msg);
+void clear_error();
+int fail(int code, const std::string& msg);
+// Records a CUDA error (if any) and returns SDD_ERR_CUDA, else SDD_OK.
+int cuda_status(cudaError_t e, const char* what);
+void count_launch(uint64_t k = 1);
+
+#define SDD_CUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::sdd::cuda_status(e_, #call);    \
+    } while (0)
+
+// --------------------------------------------------- per-mesh MC record --
+// One record per mesh in a Monte Carlo launch.  Parameters are read by the
+// path kernel at the start of each work item (warp-uniform loads).
+struct McStatsDev {
+    unsigned long long steps;
+    unsigned long long ties;
+    unsigned long long caps;
+    unsigned long long max_stderr_bits;   // bit pattern of a non-negative double
+};
+
+struct MeshDev {
+    int32_t n;              // grid points per side
+    int32_t family;         // SDD_FAMILY_*
+    int32_t nb;             // bumps (BUMPS family)
+    int32_t precision;      // SDD_FP64 | SDD_FP32_STEP
+    uint32_t key0, key1;    // Philox key = seed (lo, hi)
+    uint32_t paths;         // N per node
+    uint32_t chunk;         // paths per work item
+    uint32_t chunks_per_node;
+    uint32_t max_steps;     // step cap per path (< 2^32)
+    int64_t n_nodes;
+    uint64_t item_begin;    // first work item of this mesh
+    uint64_t node_begin;    // first global node of this mesh
+    double dt;
+    double sqrt2dt;
+    double tie_delta;
+    double sgn;             // +1: c = w, -1: c = 1/w
+    const int2* nodes;      // [n_nodes] (i, j)
+    const double* edges;    // [2][4][n]
+    sdd_node_sums* sums;    // [n_nodes] out
+    double* mean;           // [n_nodes][2] out (may be null)
+    double* stderr_;        // [n_nodes][2] out (may be null)
+    McStatsDev* stats;      // out
+    float pf[48];           // FP32-stepping parameters, pre-transformed per family
+    double pd[32];          // raw parameters (FP64 stepping)
+};
+
+// Partial sums of one work item (one chunk of paths of one node).
+struct Slot {
+    double s_hi[2], s_lo[2];   // sum of d over non-tie paths (compensated pair)
+    double q_hi[2], q_lo[2];   // sum of d^2 over non-tie paths
+    double st[2], qt[2];       // sums over tie-flagged paths
+    uint32_t ties, caps;
+    unsigned long long steps;
+};
+
+// Fills the family-specific FP32 parameter block of a mesh record.
+void fill_fp32_params(MeshDev& m, const sdd_density& d);
+
+// Arguments of a Monte Carlo launch.  Batched: `meshes` points to n_meshes
+// device records and item_off / node_off to their device prefix sums
+// (n_meshes + 1 entries).  Single mesh: meshes = NULL and `single` holds the
+// record (item_begin = node_begin = 0).
+struct McArgs {
+    const MeshDev* meshes;
+    int n_meshes;
+    const uint64_t* item_off;
+    const uint64_t* node_off;
+    uint64_t total_items;
+    uint64_t total_nodes;
+    unsigned long long* queue;   // device work counter (reset by the launcher)
+    Slot* slots;                 // total_items entries
+    MeshDev single;
+};
+
+// Launches the path kernel and the per-node reduction.
+int launch_mc(const McArgs& args, int precision, cudaStream_t stream);
+
+// Persistent-grid size of the path kernel for the current device.
+int mc_grid_blocks(int precision, int* blocks, int* threads);
+
+// ------------------------------------------------------- solve records --
+struct SolveMeshDev {
+    int32_t n;
+    int32_t solver;
+    int32_t max_iter;
+    int32_t reserved;
+    double tol;
+    double omega;
+    double* u;              // [n][n][2] mesh (in/out, FP64)
+    const double* cx;       // [n][n-1]  c at (i+1/2, j)
+    const double* cy;       // [n-1][n]  c at (i, j+1/2)
+    const float* cxf;       // FP32 copies
+    const float* cyf;
+    float* work;            // FP32 workspace, 9 floats per grid node (r p q x: 2 each, 1/diag)
+};
+
+struct SubDev {
+    int32_t mesh;           // index into the SolveMeshDev array
+    int32_t i0, i1, j0, j1; // interior: i0 < i < i1, j0 < j < j1
+};
+
+struct SubStat {
+    int32_t iterations;
+    int32_t converged;
+    double rel_residual;
+};
+
+// c at edge midpoints (FP64 and FP32 copies) for one mesh.
+int launch_edge_coefs(int n, int family, int coef_mode, const double* params, double* cx,
+                      double* cy, float* cxf, float* cyf, cudaStream_t stream);
+// Boundary tables + interface values into the mesh, Coons-patch start values
+// in the subdomain interiors.
+int launch_fill_mesh(int n, const double* edges, const int2* nodes, int64_t n_nodes,
+                     const double* iface, double* u, const SubDev* subs, int n_subs,
+                     cudaStream_t stream);
+// Arguments of a solve launch: batched (`meshes` = device records) or one mesh
+// (`meshes` = NULL, record in `single`).  One CTA per entry of `subs`.
+struct SolveArgs {
+    const SolveMeshDev* meshes;
+    SolveMeshDev single;
+    const SubDev* subs;
+    int n_subs;
+    SubStat* stats;
+};
+int launch_solve(const SolveArgs& args, cudaStream_t stream);
+
+}  // namespace sdd

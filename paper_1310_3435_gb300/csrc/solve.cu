@@ -1,0 +1,481 @@
+// Subdomain solves of the SDD mesh generator (Bihlo & Haynes, §2.1, Fig. 1;
+// §3.5): the interface Monte Carlo values and the boundary map are Dirichlet
+// data, and every subdomain's conservative five-point system
+//     sum_nbr c_edge (u_nbr - u_ij) = 0,   c at edge midpoints  (§3.2)
+// is solved independently, once (no iteration between subdomains).
+//
+// One CTA per subdomain, all subdomains of all meshes in one launch.  The mesh
+// u is FP64 [n][n][2] (the two components share the operator and are solved
+// together, interleaved as double2).  Two solvers:
+//   * red-black SOR in FP64;
+//   * FP32 Jacobi-preconditioned CG for the correction A d = r, wrapped in FP64
+//     iterative refinement (FP64 residual r = b - A u, u += d).
+// Each CTA iterates to its relative residual ||b - A u||_2 / ||b||_2 <= tol,
+// stagnation or the iteration cap; the loops are bounded, never spin.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sdd_internal.h"
+
+namespace sdd {
+namespace {
+
+constexpr int SOLVE_THREADS = 512;
+
+// ------------------------------------------------------ coefficients ----
+// c(s,t) = w or 1/w for the three density families, FP64.
+__device__ double coef64(int family, int coef_mode, const double* __restrict__ p, double s,
+                         double t)
+{
+    double w;
+    if (family == SDD_FAMILY_RING) {
+        const double ds = s - p[1], dtt = t - p[2];
+        const double u = p[3] * (sqrt(ds * ds + dtt * dtt) - p[4]);
+        const double e = exp(-2.0 * fabs(u));
+        const double ope = 1.0 + e;
+        w = 1.0 + p[0] * 4.0 * e / (ope * ope);           // A sech^2(u)
+    } else if (family == SDD_FAMILY_RIDGE) {
+        double sn, cn;
+        sincospi(2.0 * p[4] * s, &sn, &cn);
+        const double v = t - p[2] - p[3] * sn;
+        w = 1.0 + p[0] * exp(-p[1] * v * v);
+    } else {
+        const int nb = (int)p[0];
+        w = 1.0;
+        for (int b = 0; b < nb; ++b) {
+            const double* q = p + 1 + 5 * b;
+            const double ds = s - q[1], dtt = t - q[2];
+            w += q[0] * exp(-(q[3] * ds * ds + q[4] * dtt * dtt));
+        }
+    }
+    return coef_mode == SDD_COEF_INV_W ? 1.0 / w : w;
+}
+
+struct CoefArgs {
+    int n, family, coef_mode;
+    double p[SDD_MAX_PARAMS];
+};
+
+// cx[j][i] = c((i+1/2)h, jh), i < n-1;  cy[j][i] = c(ih, (j+1/2)h), j < n-1.
+__global__ void k_edge_coefs(CoefArgs a, double* __restrict__ cx, double* __restrict__ cy,
+                             float* __restrict__ cxf, float* __restrict__ cyf)
+{
+    const int n = a.n;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = (int64_t)n * (n - 1);
+    if (g >= 2 * m) return;
+    const double h = 1.0 / (double)(n - 1);
+    if (g < m) {
+        const int j = (int)(g / (n - 1)), i = (int)(g % (n - 1));
+        const double c = coef64(a.family, a.coef_mode, a.p, ((double)i + 0.5) * h, (double)j / (double)(n - 1));
+        cx[g] = c;
+        cxf[g] = (float)c;
+    } else {
+        const int64_t q = g - m;
+        const int j = (int)(q / n), i = (int)(q % n);
+        const double c = coef64(a.family, a.coef_mode, a.p, (double)i / (double)(n - 1), ((double)j + 0.5) * h);
+        cy[q] = c;
+        cyf[q] = (float)c;
+    }
+}
+
+// Boundary rows/columns from the tables (rows t=0 and t=1 include corners),
+// then the interface values.
+__global__ void k_fill_ring(int n, const double* __restrict__ edges, const int2* __restrict__ nodes,
+                            int64_t n_nodes, const double* __restrict__ iface,
+                            double2* __restrict__ u)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nb = 4 * (int64_t)n;
+    if (g < nb) {
+        const int e = (int)(g / n), k = (int)(g % n);
+        const double v0 = edges[(0 * 4 + e) * (int64_t)n + k];
+        const double v1 = edges[(1 * 4 + e) * (int64_t)n + k];
+        int64_t idx;
+        if (e == 0) idx = k;                                   // bottom, t = 0
+        else if (e == 1) idx = (int64_t)(n - 1) * n + k;       // top, t = 1
+        else {
+            if (k == 0 || k == n - 1) return;                  // corners from the rows
+            idx = (int64_t)k * n + (e == 2 ? 0 : n - 1);
+        }
+        u[idx] = make_double2(v0, v1);
+    } else if (g - nb < n_nodes) {
+        const int64_t v = g - nb;
+        const int2 ij = nodes[v];
+        u[(int64_t)ij.y * n + ij.x] = make_double2(iface[2 * v], iface[2 * v + 1]);
+    }
+}
+
+// Transfinite (Coons) interpolation of each subdomain's ring as the start
+// value of its interior.
+__global__ void k_coons(SolveArgs a)
+{
+    const SubDev sd = a.subs[blockIdx.x];
+    const SolveMeshDev& M = a.meshes ? a.meshes[sd.mesh] : a.single;
+    const int n = M.n;
+    double2* __restrict__ u = reinterpret_cast<double2*>(M.u);
+    const int nx = sd.i1 - sd.i0 - 1, ny = sd.j1 - sd.j0 - 1;
+    if (nx <= 0 || ny <= 0) return;
+    const double2 c00 = u[(int64_t)sd.j0 * n + sd.i0], c10 = u[(int64_t)sd.j0 * n + sd.i1];
+    const double2 c01 = u[(int64_t)sd.j1 * n + sd.i0], c11 = u[(int64_t)sd.j1 * n + sd.i1];
+    const double wi = 1.0 / (double)(sd.i1 - sd.i0), wj = 1.0 / (double)(sd.j1 - sd.j0);
+    for (int t = threadIdx.x; t < nx * ny; t += blockDim.x) {
+        const int i = sd.i0 + 1 + t % nx, j = sd.j0 + 1 + t / nx;
+        const double a = (double)(i - sd.i0) * wi, b = (double)(j - sd.j0) * wj;
+        const double2 L = u[(int64_t)j * n + sd.i0], Rr = u[(int64_t)j * n + sd.i1];
+        const double2 B = u[(int64_t)sd.j0 * n + i], T = u[(int64_t)sd.j1 * n + i];
+        double2 v;
+        v.x = (1 - a) * L.x + a * Rr.x + (1 - b) * B.x + b * T.x -
+              ((1 - a) * (1 - b) * c00.x + a * (1 - b) * c10.x + (1 - a) * b * c01.x + a * b * c11.x);
+        v.y = (1 - a) * L.y + a * Rr.y + (1 - b) * B.y + b * T.y -
+              ((1 - a) * (1 - b) * c00.y + a * (1 - b) * c10.y + (1 - a) * b * c01.y + a * b * c11.y);
+        u[(int64_t)j * n + i] = v;
+    }
+}
+
+// --------------------------------------------------- block reductions ----
+template <typename T, int K>
+__device__ void block_sum(T (&v)[K], T* scratch /* >= K * 32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+    __syncthreads();                       // scratch may still be read by a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < K; ++q) scratch[q * 32 + warp] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        T s = T(0);
+        for (int w = 0; w < nw; ++w) s += scratch[q * 32 + w];   // fixed order
+        v[q] = s;
+    }
+}
+
+struct Box {
+    int n, i0, i1, j0, j1, nx, ny;
+    __device__ Box(const SubDev& sd, int n_) : n(n_), i0(sd.i0), i1(sd.i1), j0(sd.j0), j1(sd.j1)
+    {
+        nx = i1 - i0 - 1;
+        ny = j1 - j0 - 1;
+    }
+    __device__ bool interior(int i, int j) const { return i > i0 && i < i1 && j > j0 && j < j1; }
+};
+
+// FP64 residual  r_ij = sum_nbr c (u_nbr - u_ij)  (= (b - A u)_ij) at node (i,j).
+__device__ __forceinline__ double2 residual64(const SolveMeshDev& M, const double2* __restrict__ u,
+                                              int n, int i, int j)
+{
+    const int64_t id = (int64_t)j * n + i;
+    const double cE = M.cx[(int64_t)j * (n - 1) + i], cW = M.cx[(int64_t)j * (n - 1) + i - 1];
+    const double cN = M.cy[id], cS = M.cy[id - n];
+    const double2 c = u[id], e = u[id + 1], w = u[id - 1], nn = u[id + n], s = u[id - n];
+    double2 r;
+    r.x = cE * (e.x - c.x) + cW * (w.x - c.x) + cN * (nn.x - c.x) + cS * (s.x - c.x);
+    r.y = cE * (e.y - c.y) + cW * (w.y - c.y) + cN * (nn.y - c.y) + cS * (s.y - c.y);
+    return r;
+}
+
+// ||b||^2: b_ij = sum of c u_nbr over the Dirichlet (ring) neighbours.
+__device__ double rhs_norm2(const SolveMeshDev& M, const Box& B, double* scratch)
+{
+    const int n = B.n;
+    const double2* __restrict__ u = reinterpret_cast<const double2*>(M.u);
+    double acc[1] = {0.0};
+    for (int t = threadIdx.x; t < B.nx * B.ny; t += blockDim.x) {
+        const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+        if (i != B.i0 + 1 && i != B.i1 - 1 && j != B.j0 + 1 && j != B.j1 - 1) continue;
+        const int64_t id = (int64_t)j * n + i;
+        double bx = 0.0, by = 0.0;
+        const int ni[4] = {i + 1, i - 1, i, i};
+        const int nj[4] = {j, j, j + 1, j - 1};
+        const double cc[4] = {M.cx[(int64_t)j * (n - 1) + i], M.cx[(int64_t)j * (n - 1) + i - 1],
+                              M.cy[id], M.cy[id - n]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!B.interior(ni[q], nj[q])) {
+                const double2 v = u[(int64_t)nj[q] * n + ni[q]];
+                bx += cc[q] * v.x;
+                by += cc[q] * v.y;
+            }
+        }
+        acc[0] += bx * bx + by * by;
+    }
+    block_sum<double, 1>(acc, scratch);
+    return acc[0];
+}
+
+__device__ double residual_norm2(const SolveMeshDev& M, const Box& B, double* scratch)
+{
+    const double2* __restrict__ u = reinterpret_cast<const double2*>(M.u);
+    double acc[1] = {0.0};
+    for (int t = threadIdx.x; t < B.nx * B.ny; t += blockDim.x) {
+        const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+        const double2 r = residual64(M, u, B.n, i, j);
+        acc[0] += r.x * r.x + r.y * r.y;
+    }
+    block_sum<double, 1>(acc, scratch);
+    return acc[0];
+}
+
+// ------------------------------------------------------------ SOR ----
+__device__ void sor_box(const SolveMeshDev& M, const Box& B, SubStat& st, double* scratch)
+{
+    const int n = B.n;
+    double2* __restrict__ u = reinterpret_cast<double2*>(M.u);
+    double omega = M.omega;
+    if (!(omega > 0.0 && omega < 2.0)) {
+        const double rho = 0.5 * (cospi(1.0 / (B.nx + 1)) + cospi(1.0 / (B.ny + 1)));
+        omega = 2.0 / (1.0 + sqrt(fmax(1.0 - rho * rho, 0.0)));
+    }
+    const double b2 = rhs_norm2(M, B, scratch);
+    const double goal = M.tol * M.tol * fmax(b2, 1e-300);
+    const int hx = (B.nx + 1) / 2;
+    const int max_iter = M.max_iter;
+    const int check = 8;
+    double best = INFINITY;
+    int stall = 0, it = 0;
+    double r2 = residual_norm2(M, B, scratch);
+    while (r2 > goal && it < max_iter) {
+        for (int sweep = 0; sweep < check; ++sweep, ++it) {
+#pragma unroll 1
+            for (int color = 0; color < 2; ++color) {
+                for (int t = threadIdx.x; t < B.ny * hx; t += blockDim.x) {
+                    const int j = B.j0 + 1 + t / hx;
+                    const int i = B.i0 + 1 + ((B.i0 + 1 + j + color) & 1) + 2 * (t % hx);
+                    if (i >= B.i1) continue;
+                    const int64_t id = (int64_t)j * n + i;
+                    const double cE = M.cx[(int64_t)j * (n - 1) + i];
+                    const double cW = M.cx[(int64_t)j * (n - 1) + i - 1];
+                    const double cN = M.cy[id], cS = M.cy[id - n];
+                    const double2 e = u[id + 1], w = u[id - 1], nn = u[id + n], s = u[id - n];
+                    const double2 c = u[id];
+                    const double dinv = 1.0 / (cE + cW + cN + cS);
+                    const double gx = (cE * e.x + cW * w.x + cN * nn.x + cS * s.x) * dinv;
+                    const double gy = (cE * e.y + cW * w.y + cN * nn.y + cS * s.y) * dinv;
+                    u[id] = make_double2(c.x + omega * (gx - c.x), c.y + omega * (gy - c.y));
+                }
+                __syncthreads();
+            }
+        }
+        r2 = residual_norm2(M, B, scratch);
+        if (r2 < 0.98 * best) { best = r2; stall = 0; }
+        else if (++stall >= 6) break;              // stagnated at rounding level
+    }
+    st.iterations = it;
+    st.rel_residual = sqrt(r2 / fmax(b2, 1e-300));
+    st.converged = r2 <= goal ? 1 : 0;
+}
+
+// ------------------------------------------- FP32 PCG + FP64 refinement ----
+// Workspace per grid node (floats): r(2) p(2) q(2) x(2) dinv(1) pad(1).
+struct Work {
+    float2* r; float2* p; float2* q; float2* x; float* dinv;
+};
+
+__device__ __forceinline__ Work work_of(const SolveMeshDev& M)
+{
+    const int64_t nn = (int64_t)M.n * M.n;
+    Work w;
+    w.r = reinterpret_cast<float2*>(M.work);
+    w.p = w.r + nn;
+    w.q = w.p + nn;
+    w.x = w.q + nn;
+    w.dinv = reinterpret_cast<float*>(w.x + nn);
+    return w;
+}
+
+__device__ void cg_box(const SolveMeshDev& M, const Box& B, SubStat& st, double* scratch)
+{
+    const int n = B.n;
+    double2* __restrict__ u = reinterpret_cast<double2*>(M.u);
+    const Work W = work_of(M);
+    const float* __restrict__ cxf = M.cxf;
+    const float* __restrict__ cyf = M.cyf;
+    const int m = B.nx * B.ny;
+    float* fs = reinterpret_cast<float*>(scratch);
+
+    // p = 0 on the ring: the SpMV reads it at the interior's neighbours.
+    for (int t = threadIdx.x; t < 2 * (B.nx + B.ny) + 4; t += blockDim.x) {
+        int i, j;
+        if (t < B.nx + 2) { i = B.i0 + t; j = B.j0; }
+        else if (t < 2 * (B.nx + 2)) { i = B.i0 + (t - B.nx - 2); j = B.j1; }
+        else if (t < 2 * (B.nx + 2) + B.ny) { i = B.i0; j = B.j0 + 1 + (t - 2 * (B.nx + 2)); }
+        else { i = B.i1; j = B.j0 + 1 + (t - 2 * (B.nx + 2) - B.ny); }
+        W.p[(int64_t)j * n + i] = make_float2(0.f, 0.f);
+    }
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+        const int64_t id = (int64_t)j * n + i;
+        const float d = cxf[(int64_t)j * (n - 1) + i] + cxf[(int64_t)j * (n - 1) + i - 1] +
+                        cyf[id] + cyf[id - n];
+        W.dinv[id] = 1.0f / d;
+    }
+    const double b2 = rhs_norm2(M, B, scratch);
+    const double goal = M.tol * M.tol * fmax(b2, 1e-300);
+    const int max_inner = M.max_iter;
+    const float inner_tol2 = 1e-10f;          // FP32 inner solve: ||r|| / ||r0|| <= 1e-5
+    int total = 0;
+    double r2 = 0.0, best = INFINITY;
+    int rounds = 0, stall = 0;
+    for (rounds = 0; rounds < 40; ++rounds) {
+        // FP64 residual, cast to FP32; x = 0; p = z = D^-1 r
+        double acc[1] = {0.0};
+        float rz[2] = {0.f, 0.f};
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+            const int64_t id = (int64_t)j * n + i;
+            const double2 r = residual64(M, u, n, i, j);
+            acc[0] += r.x * r.x + r.y * r.y;
+            const float2 rf = make_float2((float)r.x, (float)r.y);
+            const float di = W.dinv[id];
+            const float2 z = make_float2(rf.x * di, rf.y * di);
+            W.r[id] = rf;
+            W.p[id] = z;
+            W.x[id] = make_float2(0.f, 0.f);
+            rz[0] += rf.x * z.x;
+            rz[1] += rf.y * z.y;
+        }
+        block_sum<double, 1>(acc, scratch);
+        r2 = acc[0];
+        if (r2 <= goal) break;
+        if (r2 < 0.5 * best) { best = r2; stall = 0; }
+        else if (++stall >= 3) break;          // refinement no longer gains
+        block_sum<float, 2>(rz, fs + 64);
+        const float rz0 = fmaxf(rz[0], rz[1]);
+        float rzc[2] = {rz[0], rz[1]};
+        int it = 0;
+        for (; it < max_inner; ++it) {
+            __syncthreads();                   // p complete before the SpMV
+            float pq[2] = {0.f, 0.f};
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+                const int64_t id = (int64_t)j * n + i;
+                const float cE = cxf[(int64_t)j * (n - 1) + i], cW = cxf[(int64_t)j * (n - 1) + i - 1];
+                const float cN = cyf[id], cS = cyf[id - n];
+                const float2 c = W.p[id], e = W.p[id + 1], w = W.p[id - 1];
+                const float2 nn = W.p[id + n], s = W.p[id - n];
+                const float d = cE + cW + cN + cS;
+                float2 q;
+                q.x = d * c.x - (cE * e.x + cW * w.x + cN * nn.x + cS * s.x);
+                q.y = d * c.y - (cE * e.y + cW * w.y + cN * nn.y + cS * s.y);
+                W.q[id] = q;
+                pq[0] += c.x * q.x;
+                pq[1] += c.y * q.y;
+            }
+            block_sum<float, 2>(pq, fs);
+            const float al0 = pq[0] > 0.f ? rzc[0] / pq[0] : 0.f;
+            const float al1 = pq[1] > 0.f ? rzc[1] / pq[1] : 0.f;
+            float nz[2] = {0.f, 0.f};
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+                const int64_t id = (int64_t)j * n + i;
+                const float2 p = W.p[id], q = W.q[id];
+                float2 x = W.x[id], r = W.r[id];
+                x.x += al0 * p.x; x.y += al1 * p.y;
+                r.x -= al0 * q.x; r.y -= al1 * q.y;
+                W.x[id] = x;
+                W.r[id] = r;
+                const float di = W.dinv[id];
+                nz[0] += r.x * r.x * di;
+                nz[1] += r.y * r.y * di;
+            }
+            block_sum<float, 2>(nz, fs + 64);
+            const float be0 = rzc[0] > 0.f ? nz[0] / rzc[0] : 0.f;
+            const float be1 = rzc[1] > 0.f ? nz[1] / rzc[1] : 0.f;
+            rzc[0] = nz[0];
+            rzc[1] = nz[1];
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+                const int64_t id = (int64_t)j * n + i;
+                const float di = W.dinv[id];
+                const float2 r = W.r[id], p = W.p[id];
+                W.p[id] = make_float2(r.x * di + be0 * p.x, r.y * di + be1 * p.y);
+            }
+            if (fmaxf(rzc[0], rzc[1]) <= inner_tol2 * rz0) { ++it; break; }
+        }
+        total += it;
+        __syncthreads();
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+            const int64_t id = (int64_t)j * n + i;
+            const float2 x = W.x[id];
+            double2 v = u[id];
+            v.x += (double)x.x;
+            v.y += (double)x.y;
+            u[id] = v;
+        }
+        __syncthreads();
+    }
+    st.iterations = total;
+    st.rel_residual = sqrt(r2 / fmax(b2, 1e-300));
+    st.converged = r2 <= goal ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(SOLVE_THREADS)
+k_solve(SolveArgs a)
+{
+    __shared__ double scratch[128];
+    const SubDev sd = a.subs[blockIdx.x];
+    const SolveMeshDev& M = a.meshes ? a.meshes[sd.mesh] : a.single;
+    const Box B(sd, M.n);
+    SubStat st;
+    st.iterations = 0;
+    st.converged = 1;
+    st.rel_residual = 0.0;
+    if (B.nx > 0 && B.ny > 0) {
+        if (M.solver == SDD_SOLVER_CG_FP32_REFINE) cg_box(M, B, st, scratch);
+        else sor_box(M, B, st, scratch);
+    }
+    if (threadIdx.x == 0) a.stats[blockIdx.x] = st;
+}
+
+}  // namespace
+
+int launch_edge_coefs(int n, int family, int coef_mode, const double* params, double* cx,
+                      double* cy, float* cxf, float* cyf, cudaStream_t stream)
+{
+    CoefArgs a;
+    a.n = n;
+    a.family = family;
+    a.coef_mode = coef_mode;
+    for (int q = 0; q < SDD_MAX_PARAMS; ++q) a.p[q] = params[q];
+    const int64_t total = 2 * (int64_t)n * (n - 1);
+    k_edge_coefs<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, cx, cy, cxf, cyf);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
+
+int launch_fill_mesh(int n, const double* edges, const int2* nodes, int64_t n_nodes,
+                     const double* iface, double* u, const SubDev* subs, int n_subs,
+                     cudaStream_t stream)
+{
+    (void)subs;
+    (void)n_subs;
+    const int64_t total = 4 * (int64_t)n + n_nodes;
+    k_fill_ring<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
+        n, edges, nodes, n_nodes, iface, reinterpret_cast<double2*>(u));
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
+
+int launch_solve(const SolveArgs& args, cudaStream_t stream)
+{
+    if (args.n_subs <= 0) return SDD_OK;
+    k_coons<<<args.n_subs, 256, 0, stream>>>(args);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    k_solve<<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
+
+}  // namespace sdd
