@@ -112,8 +112,9 @@ def test_edge_cases(orc):
     o = oracle_sums(orc, spec)
     assert g.shape == (1,)
     _compare_fp64(orc, spec, g, o, orc.interface_nodes(3, 2, 2))
-    # every path capped
-    spec = W.config1(paths=100, max_steps=3)
+    # every path capped: 3 steps of size sqrt(2e-7) cannot reach a side from
+    # the nearest interface node (distance 1/32)
+    spec = W.config1(paths=100, max_steps=3, dt=1e-7)
     g = gpu_sums(spec)
     assert np.all(g["non_exits"] == 100) and np.all(g["steps"] == 300)
     o = oracle_sums(orc, spec)
