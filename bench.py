@@ -198,7 +198,10 @@ def run_native(args):
     dev = torch.device("cuda", local)
     spec = make_spec(args.config)
     # independent problem per rank: its own seed (weak scaling, no collective)
-    spec = W.MeshSpec(**{**spec.__dict__, "seed": spec.seed + 1000003 * rank})
+    over = {"seed": spec.seed + 1000003 * rank}
+    if args.paths:
+        over["paths"] = args.paths
+    spec = W.MeshSpec(**{**spec.__dict__, **over})
     stream = torch.cuda.Stream(device=dev)
     plan = N.Plan(spec)
     mc = plan.mc_params(precision=spec.precision if args.precision is None else args.precision)
@@ -286,6 +289,7 @@ def run_native(args):
     t_mc = sum(ms_mc) / len(ms_mc) / 1000.0
     achieved = OPS_PER_STEP_RING_FP32 * path_steps / t_mc / 1e9
     line = {
+        "mc_path_steps_per_s": achieved_steps_per_s(path_steps, t_mc),
         "metric": "SDE path-steps/s",
         "step": "one whole mesh generation: interface Monte Carlo + subdomain solves",
         "value": value, "unit": "path-steps/s", "n_gpus": world, "steps": args.steps,
@@ -312,6 +316,10 @@ def run_native(args):
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_fp64:
+        line["fp64_gpu"] = fp64_leg(N, spec, stream, dev, args.fp64_paths)
+        line["fp32_over_fp64"] = line["fp64_gpu"]["comparable_value"] and (
+            achieved_steps_per_s(path_steps, t_mc) / line["fp64_gpu"]["comparable_value"])
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = {k: v for k, v in oracle_sample(spec, budget_s=args.ref_budget).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}
@@ -322,6 +330,34 @@ def run_native(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def achieved_steps_per_s(path_steps, seconds):
+    return path_steps / seconds
+
+
+def fp64_leg(N, spec, stream, dev, paths):
+    """Plain FP64 stepping on the GPU, same workload geometry and streams, on
+    the first `paths` paths of every node (FP64 is far slower on this part):
+    the interface Monte Carlo's path-steps/s, comparable with the FP32 path
+    kernel's rate (path-steps/s is per unit of work)."""
+    import torch
+    sub = W.MeshSpec(**{**spec.__dict__, "paths": paths, "precision": W.FP64})
+    with N.Plan(sub) as P:
+        mc = P.mc_params()
+        N.sdd_interface_mc(P.handle, mc, want_stats=False, stream=stream)      # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        N.sdd_interface_mc(P.handle, mc, want_stats=False, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = N.sdd_plan_last_mc_stats(P.handle)
+        sec = e0.elapsed_time(e1) / 1000.0
+    return {"paths_per_node": paths, "path_steps": int(st.path_steps), "seconds": sec,
+            "comparable_value": st.path_steps / sec, "unit": "path-steps/s",
+            "note": "interface Monte Carlo only, FP64 stepping"}
 
 
 def main(argv=None):
@@ -336,6 +372,11 @@ def main(argv=None):
                     help="seconds of CPU work per oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--fp64-paths", type=int, default=2048,
+                    help="paths per node of the plain-FP64 GPU comparison leg")
+    ap.add_argument("--paths", type=int, default=0,
+                    help="override paths per node (profiling runs on a small case)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
