@@ -204,7 +204,8 @@ def run_native(args):
     spec = W.MeshSpec(**{**spec.__dict__, **over})
     stream = torch.cuda.Stream(device=dev)
     plan = N.Plan(spec)
-    mc = plan.mc_params(precision=spec.precision if args.precision is None else args.precision)
+    mc = plan.mc_params(precision=spec.precision if args.precision is None else args.precision,
+                        chunk=args.chunk)
     sp = plan.solve_params()
     n = spec.n
     mesh = torch.zeros((n, n, 2), dtype=torch.float64, device=dev)
@@ -375,6 +376,7 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-paths", type=int, default=2048,
                     help="paths per node of the plain-FP64 GPU comparison leg")
+    ap.add_argument("--chunk", type=int, default=0, help="paths per work item (0: automatic)")
     ap.add_argument("--paths", type=int, default=0,
                     help="override paths per node (profiling runs on a small case)")
     args = ap.parse_args(argv)

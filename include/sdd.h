@@ -114,7 +114,8 @@ typedef struct {
     double dt;                         /* Euler-Maruyama step, > 0 */
     uint64_t seed;                     /* Philox4x32-10 key (lo, hi words) */
     int32_t precision;                 /* SDD_FP64 | SDD_FP32_STEP */
-    int32_t chunk;                     /* paths per work item, 0 = automatic */
+    int32_t chunk;                     /* paths per work item: 0 = automatic, else a
+                                          multiple of 32, at most 8192 */
     uint64_t max_steps;                /* step cap per path, 0 = ceil(2/dt) */
     double tie_delta;                  /* <0: default (1e-11 FP64, 0 FP32) */
 } sdd_mc_params;

@@ -50,15 +50,20 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, extra_flags: list | None = None, verbose: bool = False) -> str:
-    if not force and not extra_flags and up_to_date():
+def build(force: bool = False, extra_flags: list | None = None, verbose: bool = False,
+          out_dir: str | None = None) -> str:
+    """Compiles libsdd.so into `out_dir` (default: the package's _build/) with
+    optional extra nvcc flags (e.g. -D tuning macros)."""
+    if not force and not extra_flags and out_dir is None and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = out_dir or BUILD
+    lib_path = os.path.join(build_dir, "libsdd.so")
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     flags = ARCH + NVCC_FLAGS + list(extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -70,13 +75,13 @@ def build(force: bool = False, extra_flags: list | None = None, verbose: bool = 
     srcs = sources()
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

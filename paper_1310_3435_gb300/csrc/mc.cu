@@ -29,9 +29,10 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MC_THREADS = 256;
 // Minimum resident blocks per SM requested from the register allocator: the
-// FP32-stepping kernel fits 80 registers without spills at 3 blocks of 256.
+// FP32-stepping kernel runs fastest at 4 blocks of 256 (64 registers; the
+// spills are in the rare refill and exit code).
 #ifndef SDD_MC_MIN_BLOCKS_F32
-#define SDD_MC_MIN_BLOCKS_F32 3
+#define SDD_MC_MIN_BLOCKS_F32 4
 #endif
 #ifndef SDD_MC_MIN_BLOCKS_F64
 #define SDD_MC_MIN_BLOCKS_F64 1
@@ -366,7 +367,7 @@ __device__ __forceinline__ void acc_add(AccSmem& A, int tid, double d0, double d
 
 // Butterfly over the warp of the lane sums; lane 0 writes the item's slot.
 __device__ void acc_write_slot(const AccSmem& A, int tid, int lane, uint32_t ties, uint32_t caps,
-                               unsigned long long steps, Slot* __restrict__ out)
+                               unsigned long long steps, uint32_t paths, Slot* __restrict__ out)
 {
     double v[12];
 #pragma unroll
@@ -387,6 +388,7 @@ __device__ void acc_write_slot(const AccSmem& A, int tid, int lane, uint32_t tie
         ties += __shfl_xor_sync(FULL, ties, off);
         caps += __shfl_xor_sync(FULL, caps, off);
         steps += __shfl_xor_sync(FULL, steps, off);
+        paths += __shfl_xor_sync(FULL, paths, off);
     }
     if (lane == 0) {
         Slot sl;
@@ -399,6 +401,9 @@ __device__ void acc_write_slot(const AccSmem& A, int tid, int lane, uint32_t tie
         sl.ties = ties;
         sl.caps = caps;
         sl.steps = steps;
+        sl.paths = paths;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) sl.fx_s[c] = sl.fx_q[c] = 0;
         *out = sl;
     }
 }
@@ -406,13 +411,37 @@ __device__ void acc_write_slot(const AccSmem& A, int tid, int lane, uint32_t tie
 template <int PREC> struct RealOf { using T = double; };
 template <> struct RealOf<SDD_FP32_STEP> { using T = float; };
 
+// Philox keys.  Batched launches carry one key per mesh and advance it by the
+// Weyl constants round by round; single-mesh launches take the ten round
+// keys precomputed on the host from the kernel parameters, so they enter the
+// xors as constant operands.
+struct RegKeys {
+    uint32_t k0, k1;
+    __device__ __forceinline__ uint4 operator()(uint4 x) const { return philox4x32_10(x, k0, k1); }
+};
+struct ParamKeys {
+    const uint32_t (&rk)[20];
+    __device__ __forceinline__ uint4 operator()(uint4 x) const
+    {
+        const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
+            const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
+            x = make_uint4(hi1 ^ x.y ^ rk[2 * r], lo1, hi0 ^ x.w ^ rk[2 * r + 1], lo0);
+        }
+        return x;
+    }
+};
+
 // ------------------------------------------------------- one work item ----
 // Runs the paths of chunk `chunk` of node `node`; lanes refill from the chunk
-// in lane order as their paths end.  Two Euler-Maruyama steps per Philox call.
-template <int PREC, class Dens>
-__device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uint32_t node,
-                                         uint32_t chunk, Slot* __restrict__ out, AccSmem& A,
-                                         int tid, int lane)
+// in lane order as their paths end.  Two Euler-Maruyama steps per Philox call;
+// the step cap is tested once per pair except in the pair that reaches it.
+template <int PREC, class Dens, class Keys>
+__device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, const Keys& philox,
+                                         uint32_t node, uint32_t chunk, Slot* __restrict__ out,
+                                         AccSmem& A, int tid, int lane)
 {
     using R = typename RealOf<PREC>::T;
     const int n = M.n;
@@ -423,7 +452,6 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
     const R dtR = (R)M.dt, sq = (R)M.sqrt2dt;
     const R delta = (R)M.tie_delta;
     const uint32_t kmax = M.max_steps;
-    const uint32_t key0 = M.key0, key1 = M.key1;
     const uint32_t p_begin = chunk * M.chunk;
     const uint32_t p_end = min(M.paths, p_begin + M.chunk);
 
@@ -434,14 +462,14 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
     R ys = s0, yt = t0;      // position after it
     uint32_t k = 0;
     bool tie = false;
-    uint32_t ties = 0, caps = 0;
+    uint32_t ties = 0, caps = 0, npaths = 0;
     unsigned long long steps = 0;
     acc_zero(A, tid);
     __syncwarp();
 
     // One Euler-Maruyama step from (xs, xt) with normals (za, zb) into
     // (ys, yt).  Returns 0 to continue, 1 on exit, 2 at the step cap.
-    auto step = [&](R za, R zb) -> int {
+    auto step = [&](R za, R zb, bool check_cap) -> int {
         R bs, bt;
         dens.drift(xs, xt, bs, bt);
         ys = xs + bs * dtR + sq * za;
@@ -452,7 +480,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
             tie = tie || (m < delta);
         }
         if ((ys <= R(0)) | (ys >= R(1)) | (yt <= R(0)) | (yt >= R(1))) return 1;
-        if (k >= kmax) return 2;
+        if (check_cap && k >= kmax) return 2;
         xs = ys;
         xt = yt;
         return 0;
@@ -461,7 +489,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
     for (;;) {
         int ended = 0;
         if (active) {
-            const uint4 r = philox4x32_10(make_uint4(k >> 1, path, node, 0u), key0, key1);
+            const uint4 r = philox(make_uint4(k >> 1, path, node, 0u));
             R z0, z1, z2, z3;
             if constexpr (PREC == SDD_FP64) {
                 box_muller_f64(r.x, r.y, z0, z1);
@@ -470,12 +498,21 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
                 box_muller_f32(r.x, r.y, z0, z1);
                 box_muller_f32(r.z, r.w, z2, z3);
             }
-            ended = step(z0, z1);
-            if (!ended) ended = step(z2, z3);
+            if (k + 2u <= kmax) {
+                ended = step(z0, z1, false);
+                if (!ended) ended = step(z2, z3, false);
+                if (!ended && k >= kmax) ended = 2;
+            } else {
+                ended = step(z0, z1, true);
+                if (!ended) ended = step(z2, z3, true);
+            }
             if (ended) {
                 R tau;
-                const int e = ended == 1 ? exit_edge<R>(xs, xt, ys, yt, tau)
-                                         : nearest_edge<R>(ys, yt, tau);
+                int e = ended == 1 ? exit_edge<R>(xs, xt, ys, yt, tau) : -1;
+                if (e < 0) {                       // step cap (or a non-finite position)
+                    e = nearest_edge<R>(ys, yt, tau);
+                    ended = 2;
+                }
                 const double td = (double)tau;
                 const double f0 = lookup(M.edges + (size_t)e * n, n, td);
                 const double f1 = lookup(M.edges + (size_t)(4 + e) * n, n, td);
@@ -483,6 +520,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
                 ties += tie ? 1u : 0u;
                 caps += ended == 2 ? 1u : 0u;
                 steps += k;
+                ++npaths;
             }
         }
         const unsigned dm = __ballot_sync(FULL, ended != 0);
@@ -501,23 +539,347 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, uin
         if (!__any_sync(FULL, active)) break;
     }
     __syncwarp();
-    acc_write_slot(A, tid, lane, ties, caps, steps, out);
+    acc_write_slot(A, tid, lane, ties, caps, steps, npaths, out);
     __syncwarp();
 }
 
-template <int PREC, class Dens>
-__device__ __forceinline__ void run_with(const MeshDev& M, uint32_t node, uint32_t chunk,
-                                         Slot* out, AccSmem& A, int tid, int lane)
+template <int PREC, class Dens, class Keys>
+__device__ __forceinline__ void run_with(const MeshDev& M, const Keys& keys, uint32_t node,
+                                         uint32_t chunk, Slot* out, AccSmem& A, int tid, int lane)
 {
     Dens d;
     d.load(M);
-    run_item<PREC, Dens>(M, d, node, chunk, out, A, tid, lane);
+    run_item<PREC, Dens, Keys>(M, d, keys, node, chunk, out, A, tid, lane);
+}
+
+template <int PREC, class Keys>
+__device__ __forceinline__ void dispatch(const MeshDev& M, const Keys& keys, uint32_t node,
+                                         uint32_t chunk, Slot* out, AccSmem& A, int tid, int lane)
+{
+    if constexpr (PREC == SDD_FP64) {
+        switch (M.family) {
+            case SDD_FAMILY_RING: run_with<PREC, RingF64>(M, keys, node, chunk, out, A, tid, lane); break;
+            case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF64>(M, keys, node, chunk, out, A, tid, lane); break;
+            default: run_with<PREC, BumpsF64>(M, keys, node, chunk, out, A, tid, lane); break;
+        }
+    } else {
+        switch (M.family) {
+            case SDD_FAMILY_RING: run_with<PREC, RingF32>(M, keys, node, chunk, out, A, tid, lane); break;
+            case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF32>(M, keys, node, chunk, out, A, tid, lane); break;
+            default:
+                if (M.nb <= 1) run_with<PREC, BumpsF32<1>>(M, keys, node, chunk, out, A, tid, lane);
+                else if (M.nb == 2) run_with<PREC, BumpsF32<2>>(M, keys, node, chunk, out, A, tid, lane);
+                else if (M.nb == 3) run_with<PREC, BumpsF32<3>>(M, keys, node, chunk, out, A, tid, lane);
+                else run_with<PREC, BumpsF32<SDD_MAX_BUMPS>>(M, keys, node, chunk, out, A, tid, lane);
+                break;
+        }
+    }
+}
+
+// ----------------------------------------- FP32 stepping: path streams ----
+// In FP32 stepping the lanes of a warp stream through consecutive work items
+// of one mesh: when an item has handed out all its paths, the lanes that
+// free up start paths of the next item while the others finish theirs, so no
+// lane waits for the slowest path of an item.  Each item's sums live in one
+// of four per-warp accumulator sets in shared memory until its last path has
+// ended, then the set is written to the item's slot.  Scores enter the sums
+// as 2^-40 fixed-point integers (|d| <= 1, so an item of at most 8192 paths
+// stays below 2^53 and converts to FP64 exactly), which makes every item's
+// sums exact and independent of which lane ran which path.
+constexpr int N_SETS = 4;
+constexpr double FX_SCALE = 1099511627776.0;        // 2^40
+
+struct WarpAcc {
+    unsigned long long s[N_SETS][2];    // sum of d, fixed point
+    unsigned long long q[N_SETS][2];    // sum of d^2, fixed point
+    unsigned long long steps[N_SETS];
+    unsigned int caps[N_SETS];
+    unsigned int paths[N_SETS];
+    // warp-uniform bookkeeping of the stream (read by every lane, written by lane 0)
+    unsigned long long set_item[N_SETS];
+    unsigned int set_live[N_SETS];      // lanes running a path of the set's item
+    unsigned int used;                  // bit s: set s holds an open item
+    int cur;                            // set of the item being handed out, -1: none
+    unsigned int cur_cursor, cur_end, cur_node;
+    unsigned long long held;            // taken from the queue, not opened yet
+    unsigned long long pending;         // first item that is not this mesh's
+    int held_valid, have_pending;
+};
+
+__device__ __forceinline__ void set_zero(WarpAcc& W, int s, int lane)
+{
+    if (lane < 2) { W.s[s][lane] = 0ull; W.q[s][lane] = 0ull; }
+    if (lane == 2) W.steps[s] = 0ull;
+    if (lane == 3) { W.caps[s] = 0u; W.paths[s] = 0u; }
+}
+
+__device__ __forceinline__ void set_flush(const WarpAcc& W, int s, Slot* __restrict__ out, int lane)
+{
+    if (lane == 0) {
+        Slot sl;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            sl.s_hi[c] = sl.s_lo[c] = sl.q_hi[c] = sl.q_lo[c] = sl.st[c] = sl.qt[c] = 0.0;
+            sl.fx_s[c] = (long long)W.s[s][c];
+            sl.fx_q[c] = (long long)W.q[s][c];
+        }
+        sl.ties = 0u;
+        sl.caps = W.caps[s];
+        sl.paths = W.paths[s];
+        sl.steps = W.steps[s];
+        sl.reserved = 0u;
+        *out = sl;
+    }
+}
+
+// Rare part of the stream loop, run by the whole warp when paths have ended:
+// releases the ended lanes (mask dm), writes out the sets whose item is
+// finished, and hands new paths to idle lanes (opening the next items from
+// the queue as needed).  The new path of a lane is returned through
+// the returned record (given = lanes that received a path).
+struct Refill {
+    unsigned given;
+    uint32_t path, node;
+    int set;
+};
+
+#ifndef SDD_REFILL_INLINE
+#define SDD_REFILL_INLINE __noinline__
+#endif
+__device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs& a, WarpAcc& W,
+                                                  int lane, unsigned dm, unsigned idle,
+                                                  unsigned long long mesh_end)
+{
+    Refill out{0u, 0u, 0u, 0};
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t C = M.chunk, cpn = M.chunks_per_node, N = M.paths;
+    __syncwarp();
+    unsigned live[N_SETS];
+#pragma unroll
+    for (int s = 0; s < N_SETS; ++s) live[s] = W.set_live[s] & ~dm;
+    unsigned used = W.used;
+    int cur = W.cur;
+    uint32_t cursor = W.cur_cursor, end = W.cur_end, cnode = W.cur_node;
+    unsigned long long held = W.held, pending = W.pending;
+    bool held_valid = W.held_valid != 0, have_pending = W.have_pending != 0;
+    __syncwarp();
+    // close the sets whose item has no path left to hand out or running
+#pragma unroll
+    for (int s = 0; s < N_SETS; ++s) {
+        if (((used >> s) & 1u) && live[s] == 0u && !(s == cur && cursor < end)) {
+            set_flush(W, s, a.slots + W.set_item[s], lane);
+            used &= ~(1u << s);
+            if (s == cur) cur = -1;
+        }
+    }
+    __syncwarp();
+    unsigned given = 0u;
+    unsigned want = idle;
+    while (want) {
+        if (cur < 0 || cursor >= end) {
+            if (!held_valid) {
+                if (have_pending) break;
+                unsigned long long it = 0;
+                if (lane == 0) it = atomicAdd(a.queue, 1ull);
+                it = __shfl_sync(FULL, it, 0);
+                if (it >= a.total_items || it >= mesh_end) {
+                    pending = it;
+                    have_pending = true;
+                    break;
+                }
+                held = it;
+                held_valid = true;
+            }
+            const unsigned freeb = ~used & ((1u << N_SETS) - 1u);
+            if (!freeb) break;                         // all sets busy: wait for a flush
+            const int s = __ffs(freeb) - 1;
+            set_zero(W, s, lane);
+            if (lane == 0) W.set_item[s] = held;
+            __syncwarp();
+            used |= 1u << s;
+#pragma unroll
+            for (int q = 0; q < N_SETS; ++q)
+                if (q == s) live[q] = 0u;
+            cur = s;
+            const unsigned long long local = held - M.item_begin;
+            cnode = (uint32_t)(local / cpn);
+            cursor = (uint32_t)(local % cpn) * C;
+            end = min(N, cursor + C);
+            held_valid = false;
+        }
+        const uint32_t avail = end - cursor;
+        const unsigned r = __popc(want & lt);
+        const bool mine = ((want >> lane) & 1u) && r < avail;
+        const unsigned taken = __ballot_sync(FULL, mine);
+        if (mine) {
+            out.path = cursor + r;
+            out.node = cnode;
+            out.set = cur;
+        }
+#pragma unroll
+        for (int q = 0; q < N_SETS; ++q)
+            if (q == cur) live[q] |= taken;
+        cursor += (uint32_t)__popc(taken);
+        want &= ~taken;
+        given |= taken;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < N_SETS; ++s) W.set_live[s] = live[s];
+        W.used = used;
+        W.cur = cur;
+        W.cur_cursor = cursor;
+        W.cur_end = end;
+        W.cur_node = cnode;
+        W.held = held;
+        W.pending = pending;
+        W.held_valid = held_valid ? 1 : 0;
+        W.have_pending = have_pending ? 1 : 0;
+    }
+    __syncwarp();
+    out.given = given;
+    return out;
+}
+
+// Streams the items of mesh M starting at `first` (already taken from the
+// queue).  Returns the first item taken that is not M's (the next mesh's, or
+// >= total_items when the queue is exhausted).
+template <class Dens, class Keys>
+__device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const Dens& dens,
+                                                         const Keys& philox,
+                                                         unsigned long long first,
+                                                         const McArgs& a, WarpAcc& W, int lane)
+{
+    const int n = M.n;
+    const double invd = 1.0 / (double)(n - 1);
+    const float invf = (float)invd;
+    const float dtR = (float)M.dt, sq = (float)M.sqrt2dt;
+    const uint32_t kmax = M.max_steps;
+    const unsigned long long mesh_end = M.item_begin + (unsigned long long)M.n_nodes * M.chunks_per_node;
+
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < N_SETS; ++s) W.set_live[s] = 0u;
+        W.used = 0u;
+        W.cur = -1;
+        W.cur_cursor = W.cur_end = W.cur_node = 0u;
+        W.held = first;
+        W.held_valid = 1;
+        W.pending = 0ull;
+        W.have_pending = 0;
+    }
+    __syncwarp();
+
+    float xs = 0.f, xt = 0.f, ys = 0.f, yt = 0.f;
+    uint32_t k = 0, path = 0, node = 0;
+    int set = 0;
+    bool active = false;
+
+    auto step = [&](float za, float zb) -> bool {
+        float bs, bt;
+        dens.drift(xs, xt, bs, bt);
+        ys = xs + bs * dtR + sq * za;
+        yt = xt + bt * dtR + sq * zb;
+        ++k;
+        if ((ys <= 0.f) | (ys >= 1.f) | (yt <= 0.f) | (yt >= 1.f)) return true;
+        xs = ys;
+        xt = yt;
+        return false;
+    };
+
+    // `need` is warp-uniform: the refill runs once at the start and then only
+    // after some path ended (only an ended path can free a lane, close a set or
+    // change what can be handed out).
+    unsigned dm = 0u;
+    bool need = true;
+    for (int guard = 0;;) {
+        if (need) {
+            need = false;
+            const unsigned idle = __ballot_sync(FULL, !active);
+            const Refill rf = stream_refill(M, a, W, lane, dm, idle, mesh_end);
+            dm = 0u;
+            if ((rf.given >> lane) & 1u) {
+                path = rf.path;
+                node = rf.node;
+                set = rf.set;
+                const int2 ij = M.nodes[node];
+                xs = (float)ij.x * invf;
+                xt = (float)ij.y * invf;
+                k = 0;
+                active = true;
+            }
+            if (!__any_sync(FULL, active)) {
+                // nothing running: this mesh is done once every set is written out
+                if (W.have_pending && W.used == 0u) return W.pending;
+                if (++guard > 64) return a.total_items;    // cannot happen; never spin
+                need = true;
+                continue;
+            }
+        }
+        bool ended = false;
+        if (active) {
+            const uint4 r = philox(make_uint4(k >> 1, path, node, 0u));
+            float z0, z1, z2, z3;
+            box_muller_f32(r.x, r.y, z0, z1);
+            box_muller_f32(r.z, r.w, z2, z3);
+            bool out;
+            bool capped = false;
+            if (k + 2u <= kmax) {
+                out = step(z0, z1);
+                if (!out) out = step(z2, z3);
+                capped = !out && k >= kmax;
+            } else {
+                out = step(z0, z1);
+                if (!out && k < kmax) out = step(z2, z3);
+                capped = !out;
+            }
+            if (out | capped) {
+                float tau;
+                int e = out ? exit_edge<float>(xs, xt, ys, yt, tau) : -1;
+                if (e < 0) {                    // step cap (or a non-finite position)
+                    e = nearest_edge<float>(ys, yt, tau);
+                    capped = true;
+                }
+                const int2 ij = M.nodes[node];
+                const double td = (double)tau;
+                const double d0 = lookup(M.edges + (size_t)e * n, n, td) - (double)ij.x * invd;
+                const double d1 = lookup(M.edges + (size_t)(4 + e) * n, n, td) - (double)ij.y * invd;
+                atomicAdd(&W.s[set][0], (unsigned long long)__double2ll_rn(d0 * FX_SCALE));
+                atomicAdd(&W.s[set][1], (unsigned long long)__double2ll_rn(d1 * FX_SCALE));
+                atomicAdd(&W.q[set][0], (unsigned long long)__double2ll_rn(d0 * d0 * FX_SCALE));
+                atomicAdd(&W.q[set][1], (unsigned long long)__double2ll_rn(d1 * d1 * FX_SCALE));
+                atomicAdd(&W.steps[set], (unsigned long long)k);
+                atomicAdd(&W.caps[set], capped ? 1u : 0u);
+                atomicAdd(&W.paths[set], 1u);
+                active = false;
+                ended = true;
+            }
+        }
+        dm = __ballot_sync(FULL, ended);
+        need = dm != 0u;
+    }
+}
+
+template <class Keys>
+__device__ __forceinline__ unsigned long long dispatch_stream(const MeshDev& M, const Keys& keys,
+                                                              unsigned long long item,
+                                                              const McArgs& a, WarpAcc& W, int lane)
+{
+    switch (M.family) {
+        case SDD_FAMILY_RING: { RingF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+        case SDD_FAMILY_RIDGE: { RidgeF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+        default:
+            if (M.nb <= 1) { BumpsF32<1> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+            if (M.nb == 2) { BumpsF32<2> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+            if (M.nb == 3) { BumpsF32<3> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+            { BumpsF32<SDD_MAX_BUMPS> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    }
 }
 
 // ------------------------------------------------------ path kernel ----
-// Mesh record of work item `item` (batched launches: binary search of the
-// per-mesh item offsets; single-mesh launches: the record passed by value and
-// staged in shared memory by the block).
+// Mesh record of a work item: batched launches binary-search the per-mesh
+// item offsets; single-mesh launches read the record passed by value, staged
+// in shared memory by the block.
 __device__ __forceinline__ int find_mesh(const uint64_t* __restrict__ off, int n_meshes, uint64_t x)
 {
     int lo = 0, hi = n_meshes;                 // off[lo] <= x < off[hi]
@@ -530,46 +892,54 @@ __device__ __forceinline__ int find_mesh(const uint64_t* __restrict__ off, int n
 
 template <int PREC>
 __global__ void __launch_bounds__(MC_THREADS, PREC == SDD_FP64 ? SDD_MC_MIN_BLOCKS_F64 : SDD_MC_MIN_BLOCKS_F32)
-k_paths(McArgs a)
+k_paths(const __grid_constant__ McArgs a)
 {
-    __shared__ AccSmem acc;
     __shared__ MeshDev single;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    if (a.meshes == nullptr) {
+    const bool one = a.meshes == nullptr;
+    if (one) {
         const int* src = reinterpret_cast<const int*>(&a.single);
         int* dst = reinterpret_cast<int*>(&single);
         for (int q = tid; q < (int)(sizeof(MeshDev) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
         __syncthreads();
     }
-    for (;;) {
+    if constexpr (PREC == SDD_FP64) {
+        // FP64 stepping: one item at a time, compensated FP64 lane sums
+        __shared__ AccSmem acc;
+        for (;;) {
+            unsigned long long item = 0;
+            if (lane == 0) item = atomicAdd(a.queue, 1ull);
+            item = __shfl_sync(FULL, item, 0);
+            if (item >= a.total_items) return;
+            const MeshDev& M = one ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
+            const uint64_t local = item - M.item_begin;
+            const uint32_t node = (uint32_t)(local / M.chunks_per_node);
+            const uint32_t chunk = (uint32_t)(local % M.chunks_per_node);
+            Slot* out = a.slots + item;
+            if (one) {
+                const ParamKeys keys{a.rk};
+                dispatch<PREC>(M, keys, node, chunk, out, acc, tid, lane);
+            } else {
+                const RegKeys keys{M.key0, M.key1};
+                dispatch<PREC>(M, keys, node, chunk, out, acc, tid, lane);
+            }
+        }
+    } else {
+        // FP32 stepping: path streams across the items of a mesh
+        __shared__ WarpAcc wacc[MC_THREADS / 32];
+        WarpAcc& W = wacc[tid >> 5];
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.queue, 1ull);
         item = __shfl_sync(FULL, item, 0);
-        if (item >= a.total_items) return;
-        int m = 0;
-        if (a.meshes != nullptr) m = find_mesh(a.item_off, a.n_meshes, item);
-        const MeshDev& M = a.meshes != nullptr ? a.meshes[m] : single;
-        const uint64_t local = item - M.item_begin;
-        const uint32_t node = (uint32_t)(local / M.chunks_per_node);
-        const uint32_t chunk = (uint32_t)(local % M.chunks_per_node);
-        Slot* out = a.slots + item;
-        if constexpr (PREC == SDD_FP64) {
-            switch (M.family) {
-                case SDD_FAMILY_RING: run_with<PREC, RingF64>(M, node, chunk, out, acc, tid, lane); break;
-                case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF64>(M, node, chunk, out, acc, tid, lane); break;
-                default: run_with<PREC, BumpsF64>(M, node, chunk, out, acc, tid, lane); break;
-            }
-        } else {
-            switch (M.family) {
-                case SDD_FAMILY_RING: run_with<PREC, RingF32>(M, node, chunk, out, acc, tid, lane); break;
-                case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF32>(M, node, chunk, out, acc, tid, lane); break;
-                default:
-                    if (M.nb <= 1) run_with<PREC, BumpsF32<1>>(M, node, chunk, out, acc, tid, lane);
-                    else if (M.nb == 2) run_with<PREC, BumpsF32<2>>(M, node, chunk, out, acc, tid, lane);
-                    else if (M.nb == 3) run_with<PREC, BumpsF32<3>>(M, node, chunk, out, acc, tid, lane);
-                    else run_with<PREC, BumpsF32<SDD_MAX_BUMPS>>(M, node, chunk, out, acc, tid, lane);
-                    break;
+        while (item < a.total_items) {
+            const MeshDev& M = one ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
+            if (one) {
+                const ParamKeys keys{a.rk};
+                item = dispatch_stream(M, keys, item, a, W, lane);
+            } else {
+                const RegKeys keys{M.key0, M.key1};
+                item = dispatch_stream(M, keys, item, a, W, lane);
             }
         }
     }
@@ -580,7 +950,7 @@ k_paths(McArgs a)
 // (compensated), then mean = X0 + S/N and stderr = sqrt((Q - S^2/N)/(N(N-1)))
 // (§2.2), and the mesh's counters are accumulated (integer atomics and an
 // atomic max of the non-negative stderr bit pattern: order-independent).
-__global__ void __launch_bounds__(256) k_reduce(McArgs a)
+__global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ McArgs a)
 {
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.total_nodes) return;
@@ -592,20 +962,29 @@ __global__ void __launch_bounds__(256) k_reduce(McArgs a)
     double sh[2] = {0, 0}, sl[2] = {0, 0}, qh[2] = {0, 0}, ql[2] = {0, 0};
     double st[2] = {0, 0}, qt[2] = {0, 0};
     unsigned long long ties = 0, caps = 0, steps = 0;
+    unsigned long long paths = 0;
+    const bool fixed = M.precision == SDD_FP32_STEP;
     for (uint32_t c = 0; c < M.chunks_per_node; ++c) {
         const Slot& S = a.slots[base + c];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            sl[q] += S.s_lo[q];
-            two_sum_add(sh[q], sl[q], S.s_hi[q]);
-            ql[q] += S.q_lo[q];
-            two_sum_add(qh[q], ql[q], S.q_hi[q]);
-            st[q] += S.st[q];
-            qt[q] += S.qt[q];
+            if (fixed) {
+                // exact: |fx| < 2^53
+                two_sum_add(sh[q], sl[q], (double)S.fx_s[q] * (1.0 / FX_SCALE));
+                two_sum_add(qh[q], ql[q], (double)S.fx_q[q] * (1.0 / FX_SCALE));
+            } else {
+                sl[q] += S.s_lo[q];
+                two_sum_add(sh[q], sl[q], S.s_hi[q]);
+                ql[q] += S.q_lo[q];
+                two_sum_add(qh[q], ql[q], S.q_hi[q]);
+                st[q] += S.st[q];
+                qt[q] += S.qt[q];
+            }
         }
         ties += S.ties;
         caps += S.caps;
         steps += S.steps;
+        paths += S.paths;
     }
     const double N = (double)M.paths;
     const int2 ij = M.nodes[v];
@@ -627,7 +1006,7 @@ __global__ void __launch_bounds__(256) k_reduce(McArgs a)
         if (M.mean) M.mean[2 * v + q] = x0[q] + S / N;
         if (M.stderr_) M.stderr_[2 * v + q] = se;
     }
-    out.paths = M.paths;
+    out.paths = paths;
     out.ties = ties;
     out.non_exits = caps;
     out.steps = steps;
@@ -635,6 +1014,7 @@ __global__ void __launch_bounds__(256) k_reduce(McArgs a)
     atomicAdd(&M.stats->steps, steps);
     atomicAdd(&M.stats->ties, ties);
     atomicAdd(&M.stats->caps, caps);
+    if (paths != (unsigned long long)M.paths) atomicAdd(&M.stats->lost, 1ull);
     atomicMax(&M.stats->max_stderr_bits, (unsigned long long)__double_as_longlong(se_max));
 }
 

@@ -259,8 +259,8 @@ int validate_mc(const sdd_mc_params* mc)
         return fail(SDD_ERR_INVALID_ARG, "dt must be positive and finite");
     if (mc->precision != SDD_FP64 && mc->precision != SDD_FP32_STEP)
         return fail(SDD_ERR_INVALID_ARG, "unknown precision");
-    if (mc->chunk < 0 || (mc->chunk > 0 && mc->chunk % 32 != 0))
-        return fail(SDD_ERR_INVALID_ARG, "chunk must be 0 or a positive multiple of 32");
+    if (mc->chunk < 0 || mc->chunk > 8192 || (mc->chunk > 0 && mc->chunk % 32 != 0))
+        return fail(SDD_ERR_INVALID_ARG, "chunk must be 0 or a multiple of 32 up to 8192");
     const double cap = mc->max_steps ? (double)mc->max_steps : std::ceil(2.0 / mc->dt);
     if (cap < 1.0 || cap > 4294967294.0)
         return fail(SDD_ERR_INVALID_ARG, "max_steps must be in [1, 2^32 - 2]");
@@ -303,6 +303,10 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     m.stderr_ = stderr_dev ? stderr_dev : p->d_stderr;
     m.stats = p->d_stats;
     fill_fp32_params(m, p->dens);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[2 * r] = m.key0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[2 * r + 1] = m.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     a.meshes = nullptr;
     a.n_meshes = 1;
     a.total_items = items;
@@ -329,6 +333,8 @@ int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
     double se;
     memcpy(&se, &s.max_stderr_bits, sizeof(se));
     out->max_stderr = se;
+    if (s.lost != 0)
+        return fail(SDD_ERR_CUDA, "internal error: a node's path count differs from N");
     return SDD_OK;
 }
 

@@ -33,6 +33,7 @@ struct McStatsDev {
     unsigned long long ties;
     unsigned long long caps;
     unsigned long long max_stderr_bits;   // bit pattern of a non-negative double
+    unsigned long long lost;              // nodes whose path count differs from N (0)
 };
 
 struct MeshDev {
@@ -67,8 +68,10 @@ struct Slot {
     double s_hi[2], s_lo[2];   // sum of d over non-tie paths (compensated pair)
     double q_hi[2], q_lo[2];   // sum of d^2 over non-tie paths
     double st[2], qt[2];       // sums over tie-flagged paths
+    long long fx_s[2], fx_q[2];  // FP32 stepping: exact 2^-40 fixed-point sums of d, d^2
     uint32_t ties, caps;
     unsigned long long steps;
+    uint32_t paths, reserved;  // paths accumulated (checked against N per node)
 };
 
 // Fills the family-specific FP32 parameter block of a mesh record.
@@ -88,6 +91,7 @@ struct McArgs {
     unsigned long long* queue;   // device work counter (reset by the launcher)
     Slot* slots;                 // total_items entries
     MeshDev single;
+    uint32_t rk[20];             // single mesh: Philox round keys (k0, k1) of rounds 0..9
 };
 
 // Launches the path kernel and the per-node reduction.

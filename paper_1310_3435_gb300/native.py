@@ -104,7 +104,12 @@ def load(build_if_missing: bool = True):
     if _lib is not None:
         return _lib
     path = _build.LIB
-    if build_if_missing and not _build.up_to_date():
+    override = os.environ.get("SDD_LIBRARY")
+    if override:                        # a specific build of libsdd.so (tuning variants)
+        if not os.path.exists(override):
+            raise ImportError("SDD_LIBRARY=%s does not exist" % override)
+        path = override
+    elif build_if_missing and not _build.up_to_date():
         try:
             path = _build.build()
         except Exception as e:          # no toolchain: fail loudly, no fallback

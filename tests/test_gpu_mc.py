@@ -152,3 +152,24 @@ def test_fp32_stepping_paired_with_fp64(orc, case):
     # step counts differ only through paths whose exit decision moved
     rel_steps = abs(int(g32["steps"].sum()) - int(g64["steps"].sum())) / g64["steps"].sum()
     assert rel_steps < 1e-3
+
+
+def test_fp32_sums_are_exact_and_reproducible(orc):
+    """FP32 stepping accumulates fixed-point sums: bitwise identical across
+    runs, and across work-item sizes up to the final FP64 rounding."""
+    from paper_1310_3435_gb300 import native as N
+    spec = W.small_parity_cases()[1]
+    with gpu_plan(spec) as P:
+        mc = P.mc_params(precision=W.FP32_STEP)
+        a = N.sdd_interface_mc_sums(P.handle, mc)
+        b = N.sdd_interface_mc_sums(P.handle, mc)
+        assert a.tobytes() == b.tobytes()
+        st = N.sdd_plan_last_mc_stats(P.handle)
+        assert st.ties == 0 and st.paths == spec.paths * P.n_nodes
+        assert np.all(a["paths"] == spec.paths)
+        for chunk in (32, 64, 256, 8192):
+            c = N.sdd_interface_mc_sums(P.handle, P.mc_params(precision=W.FP32_STEP, chunk=chunk))
+            assert np.array_equal(c["steps"], a["steps"])
+            assert np.array_equal(c["paths"], a["paths"])
+            assert np.allclose(c["sum"], a["sum"], rtol=1e-15, atol=1e-12)
+            assert np.allclose(c["sumsq"], a["sumsq"], rtol=1e-15, atol=1e-12)
