@@ -29,10 +29,10 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MC_THREADS = 256;
 // Minimum resident blocks per SM requested from the register allocator: the
-// FP32-stepping kernel runs fastest at 4 blocks of 256 (64 registers; the
-// spills are in the rare refill and exit code).
+// per-family FP32-stepping kernels fit 80 registers without spills at 3
+// blocks of 256, measured fastest against 4 and 2 blocks (64, 128 registers).
 #ifndef SDD_MC_MIN_BLOCKS_F32
-#define SDD_MC_MIN_BLOCKS_F32 4
+#define SDD_MC_MIN_BLOCKS_F32 3
 #endif
 #ifndef SDD_MC_MIN_BLOCKS_F64
 #define SDD_MC_MIN_BLOCKS_F64 1
@@ -47,8 +47,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1
     const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
-        const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
+        const unsigned long long p0 = (unsigned long long)M0 * x.x;   // 32x32 -> 64
+        const unsigned long long p1 = (unsigned long long)M1 * x.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
         k0 += W0;
         k1 += W1;
@@ -96,26 +98,30 @@ __device__ __forceinline__ float cos_approx(float x)
 
 constexpr float TWO_PI_F = 6.28318530717958647692f;
 constexpr double PI_D = 3.14159265358979323846;
-constexpr float LN2_X2_F = 1.38629436111989061883f;    // 2 ln 2
 
 // Box-Muller, FP32.  Uniforms U = (floor(r / 2^9) + 1/2) 2^-23 are exact in
 // FP32 and lie in (0,1); the angle 2 pi U is taken as 2 pi (U - 1/2) + pi,
 // i.e. (cos, sin)(2 pi U) = -(cos, sin)(2 pi (U - 1/2)), which keeps the
-// argument of the hardware sine/cosine in [-pi, pi].
+// argument of the hardware sine/cosine in [-pi, pi] (the sign goes into nr).
 __device__ __forceinline__ float uniform23(uint32_t r)
 {
     // 1 + floor(r/2^9) 2^-23 in [1,2), minus (1 - 2^-24): exact.
-    return __uint_as_float((r >> 9) | 0x3f800000u) - 0.99999994039535522461f;
+    return __uint_as_float((r >> 9) + 0x3f800000u) - 0.99999994039535522461f;
 }
 
-__device__ __forceinline__ void box_muller_f32(uint32_t ra, uint32_t rb, float& z0, float& z1)
+// Box-Muller, FP32, returning the noise increment of a step in factored form:
+// sqrt(2 dt) (z0, z1) = (nr cos, nr sin), nr = -sqrt(-4 dt ln ua) and
+// (cos, sin) of 2 pi (ub - 1/2); c4dt = -4 dt ln 2.  The caller adds each
+// component with one fused multiply-add.
+__device__ __forceinline__ void box_muller_f32_step(uint32_t ra, uint32_t rb, float c4dt,
+                                                    float& nr, float& cz, float& sz)
 {
     const float ua = uniform23(ra), ub = uniform23(rb);
-    const float v = -LN2_X2_F * lg2_approx(ua);            // -2 ln ua > 0
-    const float R = v * rsqrt_approx(v);
+    const float v = c4dt * lg2_approx(ua);                  // -4 dt ln ua > 0
+    nr = -(v * rsqrt_approx(v));
     const float ang = TWO_PI_F * (ub - 0.5f);
-    z0 = -R * cos_approx(ang);
-    z1 = -R * sin_approx(ang);
+    cz = cos_approx(ang);
+    sz = sin_approx(ang);
 }
 
 // Box-Muller, FP64 with CUDA's double-precision log / sqrt / sincospi.
@@ -131,21 +137,23 @@ __device__ __forceinline__ void box_muller_f64(uint32_t ra, uint32_t rb, double&
 }
 
 // ----------------------------------------------------- densities, FP32 ----
-// Each returns b = grad ln c at (s, t), c = w^sgn.
+// Each FP32 density gives the drift half of an Euler-Maruyama step:
+// advance(s, t) = (s, t) + b dt with b = grad ln c = sgn grad(w)/w (c = w^sgn),
+// dt folded into the last multiplication.
 // BUMPS: pf[8b..8b+6] = A, cs, ct, ks log2 e, kt log2 e, -2 ks, -2 kt.
 template <int NB>
 struct BumpsF32 {
     float p[NB][7];
-    float sgn;
+    float sdt;                  // sgn * dt
     __device__ void load(const MeshDev& M)
     {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
             for (int q = 0; q < 7; ++q) p[b][q] = M.pf[8 * b + q];
-        sgn = (float)M.sgn;
+        sdt = (float)(M.sgn * M.dt);
     }
-    __device__ __forceinline__ void drift(float s, float t, float& bs, float& bt) const
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at) const
     {
         float w = 1.0f, gs = 0.0f, gt = 0.0f;
 #pragma unroll
@@ -157,9 +165,9 @@ struct BumpsF32 {
             gs = fmaf(e * p[b][5], ds, gs);
             gt = fmaf(e * p[b][6], dtt, gt);
         }
-        const float inv = sgn * rcp_approx(w);
-        bs = gs * inv;
-        bt = gt * inv;
+        const float inv = sdt * rcp_approx(w);
+        as = fmaf(gs, inv, s);
+        at = fmaf(gt, inv, t);
     }
 };
 
@@ -167,12 +175,13 @@ struct BumpsF32 {
 // With e = exp(-2|u|), u = k (r - r0):  (dw/dr) / w = -8 A k sign(u) e (1 - e)
 // / ((1 + e)((1 + e)^2 + 4 A e)), and b = sgn (dw/dr)/w (s - cs, t - ct)/r.
 struct RingF32 {
-    float cs, ct, r0, c1, A4, K;
+    float cs, ct, r0, c1, A4, Kdt;
     __device__ void load(const MeshDev& M)
     {
-        cs = M.pf[0]; ct = M.pf[1]; r0 = M.pf[2]; c1 = M.pf[3]; A4 = M.pf[4]; K = M.pf[5];
+        cs = M.pf[0]; ct = M.pf[1]; r0 = M.pf[2]; c1 = M.pf[3]; A4 = M.pf[4];
+        Kdt = (float)((double)M.pf[5] * M.dt);
     }
-    __device__ __forceinline__ void drift(float s, float t, float& bs, float& bt) const
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at) const
     {
         const float ds = s - cs, dtt = t - ct;
         const float r2 = fmaf(ds, ds, dtt * dtt);
@@ -181,10 +190,10 @@ struct RingF32 {
         const float e = ex2_approx(c1 * fabsf(u));
         const float ope = 1.0f + e;
         const float D = ope * fmaf(ope, ope, A4 * e);
-        const float num = K * copysignf(e * (1.0f - e), u) * rinv;
-        const float f = num * rcp_approx(D);
-        bs = f * ds;
-        bt = f * dtt;
+        const float num = copysignf(fmaf(-e, e, e), u) * rinv;
+        const float f = (Kdt * num) * rcp_approx(D);
+        as = fmaf(f, ds, s);
+        at = fmaf(f, dtt, t);
     }
 };
 
@@ -192,23 +201,23 @@ struct RingF32 {
 // v = t - t0 - a sin(2 pi f s); w = 1 + A exp(-k v^2);
 // dw/dt = e (-2 k v), dw/ds = dw/dt (-2 pi a f cos(2 pi f s)).
 struct RidgeF32 {
-    float A, kl, t0, a, f, m2k, m2paf, sgn;
+    float A, kl, t0, a, f, m2k, m2paf, sdt;
     __device__ void load(const MeshDev& M)
     {
         A = M.pf[0]; kl = M.pf[1]; t0 = M.pf[2]; a = M.pf[3]; f = M.pf[4];
-        m2k = M.pf[5]; m2paf = M.pf[6]; sgn = (float)M.sgn;
+        m2k = M.pf[5]; m2paf = M.pf[6]; sdt = (float)(M.sgn * M.dt);
     }
-    __device__ __forceinline__ void drift(float s, float t, float& bs, float& bt) const
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at) const
     {
         const float fr = f * s;
         const float x = TWO_PI_F * (fr - rintf(fr));           // in [-pi, pi]
         const float sn = sin_approx(x), cn = cos_approx(x);
         const float v = t - t0 - a * sn;
         const float e = A * ex2_approx(-kl * v * v);
-        const float inv = sgn * rcp_approx(1.0f + e);
+        const float inv = sdt * rcp_approx(1.0f + e);
         const float gt = e * m2k * v;
-        bt = gt * inv;
-        bs = gt * (m2paf * cn) * inv;
+        at = fmaf(gt, inv, t);
+        as = fmaf(gt * (m2paf * cn), inv, s);
     }
 };
 
@@ -426,8 +435,10 @@ struct ParamKeys {
         const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
 #pragma unroll
         for (int r = 0; r < 10; ++r) {
-            const uint32_t hi0 = __umulhi(M0, x.x), lo0 = M0 * x.x;
-            const uint32_t hi1 = __umulhi(M1, x.z), lo1 = M1 * x.z;
+            const unsigned long long p0 = (unsigned long long)M0 * x.x;
+            const unsigned long long p1 = (unsigned long long)M1 * x.z;
+            const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+            const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
             x = make_uint4(hi1 ^ x.y ^ rk[2 * r], lo1, hi0 ^ x.w ^ rk[2 * r + 1], lo0);
         }
         return x;
@@ -556,23 +567,11 @@ template <int PREC, class Keys>
 __device__ __forceinline__ void dispatch(const MeshDev& M, const Keys& keys, uint32_t node,
                                          uint32_t chunk, Slot* out, AccSmem& A, int tid, int lane)
 {
-    if constexpr (PREC == SDD_FP64) {
-        switch (M.family) {
-            case SDD_FAMILY_RING: run_with<PREC, RingF64>(M, keys, node, chunk, out, A, tid, lane); break;
-            case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF64>(M, keys, node, chunk, out, A, tid, lane); break;
-            default: run_with<PREC, BumpsF64>(M, keys, node, chunk, out, A, tid, lane); break;
-        }
-    } else {
-        switch (M.family) {
-            case SDD_FAMILY_RING: run_with<PREC, RingF32>(M, keys, node, chunk, out, A, tid, lane); break;
-            case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF32>(M, keys, node, chunk, out, A, tid, lane); break;
-            default:
-                if (M.nb <= 1) run_with<PREC, BumpsF32<1>>(M, keys, node, chunk, out, A, tid, lane);
-                else if (M.nb == 2) run_with<PREC, BumpsF32<2>>(M, keys, node, chunk, out, A, tid, lane);
-                else if (M.nb == 3) run_with<PREC, BumpsF32<3>>(M, keys, node, chunk, out, A, tid, lane);
-                else run_with<PREC, BumpsF32<SDD_MAX_BUMPS>>(M, keys, node, chunk, out, A, tid, lane);
-                break;
-        }
+    static_assert(PREC == SDD_FP64, "item-at-a-time runner serves FP64 stepping");
+    switch (M.family) {
+        case SDD_FAMILY_RING: run_with<PREC, RingF64>(M, keys, node, chunk, out, A, tid, lane); break;
+        case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF64>(M, keys, node, chunk, out, A, tid, lane); break;
+        default: run_with<PREC, BumpsF64>(M, keys, node, chunk, out, A, tid, lane); break;
     }
 }
 
@@ -753,7 +752,6 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     const int n = M.n;
     const double invd = 1.0 / (double)(n - 1);
     const float invf = (float)invd;
-    const float dtR = (float)M.dt, sq = (float)M.sqrt2dt;
     const uint32_t kmax = M.max_steps;
     const unsigned long long mesh_end = M.item_begin + (unsigned long long)M.n_nodes * M.chunks_per_node;
 
@@ -770,22 +768,11 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     }
     __syncwarp();
 
-    float xs = 0.f, xt = 0.f, ys = 0.f, yt = 0.f;
+    const float c4dt = (float)(-4.0 * M.dt * 0.69314718055994530942);
+    float xs = 0.f, xt = 0.f;
     uint32_t k = 0, path = 0, node = 0;
     int set = 0;
     bool active = false;
-
-    auto step = [&](float za, float zb) -> bool {
-        float bs, bt;
-        dens.drift(xs, xt, bs, bt);
-        ys = xs + bs * dtR + sq * za;
-        yt = xt + bt * dtR + sq * zb;
-        ++k;
-        if ((ys <= 0.f) | (ys >= 1.f) | (yt <= 0.f) | (yt >= 1.f)) return true;
-        xs = ys;
-        xt = yt;
-        return false;
-    };
 
     // `need` is warp-uniform: the refill runs once at the start and then only
     // after some path ended (only an ended path can free a lane, close a set or
@@ -818,41 +805,62 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
         }
         bool ended = false;
         if (active) {
+            // two Euler-Maruyama steps from one Philox block, both computed
+            // before the exit tests (a step after an exit is discarded)
             const uint4 r = philox(make_uint4(k >> 1, path, node, 0u));
-            float z0, z1, z2, z3;
-            box_muller_f32(r.x, r.y, z0, z1);
-            box_muller_f32(r.z, r.w, z2, z3);
-            bool out;
-            bool capped = false;
-            if (k + 2u <= kmax) {
-                out = step(z0, z1);
-                if (!out) out = step(z2, z3);
-                capped = !out && k >= kmax;
+            float na, ca, sa, nb, cb, sb;
+            box_muller_f32_step(r.x, r.y, c4dt, na, ca, sa);
+            box_muller_f32_step(r.z, r.w, c4dt, nb, cb, sb);
+            float as, at;
+            dens.advance(xs, xt, as, at);
+            const float y1s = fmaf(na, ca, as), y1t = fmaf(na, sa, at);
+            dens.advance(y1s, y1t, as, at);
+            const float y2s = fmaf(nb, cb, as), y2t = fmaf(nb, sb, at);
+            const bool out1 = (y1s <= 0.f) | (y1s >= 1.f) | (y1t <= 0.f) | (y1t >= 1.f);
+            const bool out2 = (y2s <= 0.f) | (y2s >= 1.f) | (y2t <= 0.f) | (y2t >= 1.f);
+            if (!(out1 | out2) && k + 2u < kmax) {
+                xs = y2s;
+                xt = y2t;
+                k += 2u;
             } else {
-                out = step(z0, z1);
-                if (!out && k < kmax) out = step(z2, z3);
-                capped = !out;
-            }
-            if (out | capped) {
-                float tau;
-                int e = out ? exit_edge<float>(xs, xt, ys, yt, tau) : -1;
-                if (e < 0) {                    // step cap (or a non-finite position)
-                    e = nearest_edge<float>(ys, yt, tau);
-                    capped = true;
+                // exit or step cap within this pair (rare)
+                float ps = xs, pt = xt, qs = y1s, qt = y1t;   // the step that ended
+                bool out = out1, capped = false;
+                k += 1u;
+                if (!out1) {
+                    if (k >= kmax) {
+                        capped = true;
+                    } else {
+                        ps = y1s; pt = y1t; qs = y2s; qt = y2t;
+                        out = out2;
+                        k += 1u;
+                        capped = !out2 && k >= kmax;
+                    }
                 }
-                const int2 ij = M.nodes[node];
-                const double td = (double)tau;
-                const double d0 = lookup(M.edges + (size_t)e * n, n, td) - (double)ij.x * invd;
-                const double d1 = lookup(M.edges + (size_t)(4 + e) * n, n, td) - (double)ij.y * invd;
-                atomicAdd(&W.s[set][0], (unsigned long long)__double2ll_rn(d0 * FX_SCALE));
-                atomicAdd(&W.s[set][1], (unsigned long long)__double2ll_rn(d1 * FX_SCALE));
-                atomicAdd(&W.q[set][0], (unsigned long long)__double2ll_rn(d0 * d0 * FX_SCALE));
-                atomicAdd(&W.q[set][1], (unsigned long long)__double2ll_rn(d1 * d1 * FX_SCALE));
-                atomicAdd(&W.steps[set], (unsigned long long)k);
-                atomicAdd(&W.caps[set], capped ? 1u : 0u);
-                atomicAdd(&W.paths[set], 1u);
-                active = false;
-                ended = true;
+                if (out | capped) {
+                    float tau;
+                    int e = out ? exit_edge<float>(ps, pt, qs, qt, tau) : -1;
+                    if (e < 0) {                    // step cap (or a non-finite position)
+                        e = nearest_edge<float>(qs, qt, tau);
+                        capped = true;
+                    }
+                    const int2 ij = M.nodes[node];
+                    const double td = (double)tau;
+                    const double d0 = lookup(M.edges + (size_t)e * n, n, td) - (double)ij.x * invd;
+                    const double d1 = lookup(M.edges + (size_t)(4 + e) * n, n, td) - (double)ij.y * invd;
+                    atomicAdd(&W.s[set][0], (unsigned long long)__double2ll_rn(d0 * FX_SCALE));
+                    atomicAdd(&W.s[set][1], (unsigned long long)__double2ll_rn(d1 * FX_SCALE));
+                    atomicAdd(&W.q[set][0], (unsigned long long)__double2ll_rn(d0 * d0 * FX_SCALE));
+                    atomicAdd(&W.q[set][1], (unsigned long long)__double2ll_rn(d1 * d1 * FX_SCALE));
+                    atomicAdd(&W.steps[set], (unsigned long long)k);
+                    atomicAdd(&W.caps[set], capped ? 1u : 0u);
+                    atomicAdd(&W.paths[set], 1u);
+                    active = false;
+                    ended = true;
+                } else {
+                    xs = y2s;                       // k + 2 == kmax reached without exit: next pair caps
+                    xt = y2t;
+                }
             }
         }
         dm = __ballot_sync(FULL, ended);
@@ -860,19 +868,54 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     }
 }
 
-template <class Keys>
+// Density class of a mesh: a compile-time index for the FP32 path kernel, so
+// each family gets a kernel (and a register allocation) of its own.
+enum FamClass { FC_RING = 0, FC_RIDGE, FC_BUMPS1, FC_BUMPS2, FC_BUMPS3, FC_BUMPS6, FC_ANY };
+
+__host__ __device__ __forceinline__ int fam_class(int family, int nb)
+{
+    if (family == SDD_FAMILY_RING) return FC_RING;
+    if (family == SDD_FAMILY_RIDGE) return FC_RIDGE;
+    if (nb <= 1) return FC_BUMPS1;
+    if (nb == 2) return FC_BUMPS2;
+    if (nb == 3) return FC_BUMPS3;
+    return FC_BUMPS6;
+}
+
+template <int FC, class Keys>
+__device__ __forceinline__ unsigned long long stream_fc(const MeshDev& M, const Keys& keys,
+                                                        unsigned long long item, const McArgs& a,
+                                                        WarpAcc& W, int lane)
+{
+    if constexpr (FC == FC_RING) { RingF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_RIDGE) { RidgeF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS1) { BumpsF32<1> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS2) { BumpsF32<2> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS3) { BumpsF32<3> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS6) {
+        BumpsF32<SDD_MAX_BUMPS> d;
+        d.load(M);
+        return run_stream(M, d, keys, item, a, W, lane);
+    }
+    return a.total_items;
+}
+
+template <int FC, class Keys>
 __device__ __forceinline__ unsigned long long dispatch_stream(const MeshDev& M, const Keys& keys,
                                                               unsigned long long item,
                                                               const McArgs& a, WarpAcc& W, int lane)
 {
-    switch (M.family) {
-        case SDD_FAMILY_RING: { RingF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-        case SDD_FAMILY_RIDGE: { RidgeF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-        default:
-            if (M.nb <= 1) { BumpsF32<1> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-            if (M.nb == 2) { BumpsF32<2> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-            if (M.nb == 3) { BumpsF32<3> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-            { BumpsF32<SDD_MAX_BUMPS> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC != FC_ANY) {
+        return stream_fc<FC>(M, keys, item, a, W, lane);
+    } else {
+        switch (fam_class(M.family, M.nb)) {
+            case FC_RING: return stream_fc<FC_RING>(M, keys, item, a, W, lane);
+            case FC_RIDGE: return stream_fc<FC_RIDGE>(M, keys, item, a, W, lane);
+            case FC_BUMPS1: return stream_fc<FC_BUMPS1>(M, keys, item, a, W, lane);
+            case FC_BUMPS2: return stream_fc<FC_BUMPS2>(M, keys, item, a, W, lane);
+            case FC_BUMPS3: return stream_fc<FC_BUMPS3>(M, keys, item, a, W, lane);
+            default: return stream_fc<FC_BUMPS6>(M, keys, item, a, W, lane);
+        }
     }
 }
 
@@ -890,15 +933,17 @@ __device__ __forceinline__ int find_mesh(const uint64_t* __restrict__ off, int n
     return lo;
 }
 
-template <int PREC>
+// ONE: single-mesh launch (record and round keys from the kernel parameters);
+// otherwise a batch (records in global memory, one key per mesh).  FC: the
+// density class the FP32 kernel is specialised for (FC_ANY: every class).
+template <int PREC, bool ONE, int FC>
 __global__ void __launch_bounds__(MC_THREADS, PREC == SDD_FP64 ? SDD_MC_MIN_BLOCKS_F64 : SDD_MC_MIN_BLOCKS_F32)
 k_paths(const __grid_constant__ McArgs a)
 {
     __shared__ MeshDev single;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const bool one = a.meshes == nullptr;
-    if (one) {
+    if constexpr (ONE) {
         const int* src = reinterpret_cast<const int*>(&a.single);
         int* dst = reinterpret_cast<int*>(&single);
         for (int q = tid; q < (int)(sizeof(MeshDev) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
@@ -912,12 +957,12 @@ k_paths(const __grid_constant__ McArgs a)
             if (lane == 0) item = atomicAdd(a.queue, 1ull);
             item = __shfl_sync(FULL, item, 0);
             if (item >= a.total_items) return;
-            const MeshDev& M = one ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
+            const MeshDev& M = ONE ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
             const uint64_t local = item - M.item_begin;
             const uint32_t node = (uint32_t)(local / M.chunks_per_node);
             const uint32_t chunk = (uint32_t)(local % M.chunks_per_node);
             Slot* out = a.slots + item;
-            if (one) {
+            if constexpr (ONE) {
                 const ParamKeys keys{a.rk};
                 dispatch<PREC>(M, keys, node, chunk, out, acc, tid, lane);
             } else {
@@ -933,13 +978,13 @@ k_paths(const __grid_constant__ McArgs a)
         if (lane == 0) item = atomicAdd(a.queue, 1ull);
         item = __shfl_sync(FULL, item, 0);
         while (item < a.total_items) {
-            const MeshDev& M = one ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
-            if (one) {
+            const MeshDev& M = ONE ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
+            if constexpr (ONE) {
                 const ParamKeys keys{a.rk};
-                item = dispatch_stream(M, keys, item, a, W, lane);
+                item = dispatch_stream<FC>(M, keys, item, a, W, lane);
             } else {
                 const RegKeys keys{M.key0, M.key1};
-                item = dispatch_stream(M, keys, item, a, W, lane);
+                item = dispatch_stream<FC>(M, keys, item, a, W, lane);
             }
         }
     }
@@ -1065,35 +1110,58 @@ void fill_fp32_params(MeshDev& m, const sdd_density& d)
     }
 }
 
-int mc_grid_blocks(int precision, int* blocks, int* threads)
+// Kernel of a launch: precision, single mesh or batch, density class.
+using PathKernel = void (*)(McArgs);
+
+static PathKernel path_kernel(int precision, bool one, int fc)
+{
+    if (precision == SDD_FP64) return one ? k_paths<SDD_FP64, true, FC_ANY> : k_paths<SDD_FP64, false, FC_ANY>;
+    if (!one) {
+        switch (fc) {
+            case FC_RING: return k_paths<SDD_FP32_STEP, false, FC_RING>;
+            case FC_RIDGE: return k_paths<SDD_FP32_STEP, false, FC_RIDGE>;
+            case FC_BUMPS1: return k_paths<SDD_FP32_STEP, false, FC_BUMPS1>;
+            case FC_BUMPS2: return k_paths<SDD_FP32_STEP, false, FC_BUMPS2>;
+            case FC_BUMPS3: return k_paths<SDD_FP32_STEP, false, FC_BUMPS3>;
+            case FC_BUMPS6: return k_paths<SDD_FP32_STEP, false, FC_BUMPS6>;
+            default: return k_paths<SDD_FP32_STEP, false, FC_ANY>;
+        }
+    }
+    switch (fc) {
+        case FC_RING: return k_paths<SDD_FP32_STEP, true, FC_RING>;
+        case FC_RIDGE: return k_paths<SDD_FP32_STEP, true, FC_RIDGE>;
+        case FC_BUMPS1: return k_paths<SDD_FP32_STEP, true, FC_BUMPS1>;
+        case FC_BUMPS2: return k_paths<SDD_FP32_STEP, true, FC_BUMPS2>;
+        case FC_BUMPS3: return k_paths<SDD_FP32_STEP, true, FC_BUMPS3>;
+        default: return k_paths<SDD_FP32_STEP, true, FC_BUMPS6>;
+    }
+}
+
+int mesh_fam_class(int family, int nb) { return fam_class(family, nb); }
+
+int mc_grid_blocks(int precision, int fc, bool one, int* blocks, int* threads)
 {
     int dev = 0, sms = 0, per_sm = 0;
     SDD_CUDA(cudaGetDevice(&dev));
     SDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (precision == SDD_FP64)
-        SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<SDD_FP64>,
-                                                                MC_THREADS, 0));
-    else
-        SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<SDD_FP32_STEP>,
-                                                                MC_THREADS, 0));
+    SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, reinterpret_cast<const void*>(path_kernel(precision, one, fc)), MC_THREADS, 0));
     *blocks = sms * std::max(per_sm, 1);
     *threads = MC_THREADS;
     return SDD_OK;
 }
 
-int launch_mc(const McArgs& args, int precision, cudaStream_t stream)
+int launch_mc(const McArgs& args, int precision, int fc, cudaStream_t stream)
 {
     if (args.total_items == 0) return SDD_OK;
+    const bool one = args.meshes == nullptr;
     int blocks = 0, threads = 0;
-    int rc = mc_grid_blocks(precision, &blocks, &threads);
+    int rc = mc_grid_blocks(precision, fc, one, &blocks, &threads);
     if (rc) return rc;
     const uint64_t max_blocks = (args.total_items * 32 + threads - 1) / threads;
     if ((uint64_t)blocks > max_blocks) blocks = (int)max_blocks;
     SDD_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
-    if (precision == SDD_FP64)
-        k_paths<SDD_FP64><<<blocks, threads, 0, stream>>>(args);
-    else
-        k_paths<SDD_FP32_STEP><<<blocks, threads, 0, stream>>>(args);
+    path_kernel(precision, one, fc)<<<blocks, threads, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
     const unsigned rb = (unsigned)((args.total_nodes + 255) / 256);

@@ -314,7 +314,7 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     a.queue = p->d_queue;
     a.slots = p->d_slots;
     SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
-    if ((rc = launch_mc(a, mc->precision, stream))) return rc;
+    if ((rc = launch_mc(a, mc->precision, mesh_fam_class(m.family, m.nb), stream))) return rc;
     p->last_paths = mc->paths_per_node;
     p->have_mc = true;
     p->last_stream = stream;

@@ -94,11 +94,17 @@ struct McArgs {
     uint32_t rk[20];             // single mesh: Philox round keys (k0, k1) of rounds 0..9
 };
 
-// Launches the path kernel and the per-node reduction.
-int launch_mc(const McArgs& args, int precision, cudaStream_t stream);
+// Density class of a mesh for the FP32 path kernel (one kernel per class);
+// kFamAny selects the kernel that handles every class.
+int mesh_fam_class(int family, int nb);
+constexpr int kFamAny = 6;
+
+// Launches the path kernel (for density class `fc`) and the per-node
+// reduction.
+int launch_mc(const McArgs& args, int precision, int fc, cudaStream_t stream);
 
 // Persistent-grid size of the path kernel for the current device.
-int mc_grid_blocks(int precision, int* blocks, int* threads);
+int mc_grid_blocks(int precision, int fc, bool one, int* blocks, int* threads);
 
 // ------------------------------------------------------- solve records --
 struct SolveMeshDev {

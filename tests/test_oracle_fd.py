@@ -113,3 +113,28 @@ def test_direct_solve_matches_brute_force_gauss_seidel(orc):
                 U[j, i] = (cE * U[j, i + 1] + cW * U[j, i - 1] + cN * U[j + 1, i]
                            + cS * U[j - 1, i]) / (cE + cW + cN + cS)
     assert np.max(np.abs(U - G)) < 1e-13
+
+
+def test_torsion_series_matches_a_poisson_solve(orc):
+    """The sine series of the mean exit time (Lap v = -1, v = 0 on the
+    boundary) against an independent five-point Poisson solve, extrapolated
+    in h (Richardson) to remove the O(h^2) error."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+
+    def fd_center(m):
+        h = 1.0 / (m + 1)
+        e = np.ones(m)
+        T = sp.diags([-e[:-1], 2 * e, -e[:-1]], [-1, 0, 1]) / (h * h)
+        A = sp.kronsum(T, T).tocsc()
+        v = spla.spsolve(A, np.ones(m * m))
+        return v.reshape(m, m)[m // 2, m // 2]
+
+    v1, v2 = fd_center(63), fd_center(127)
+    extrap = v2 + (v2 - v1) / 3.0
+    series = orc.torsion_exit_time(0.5, 0.5)
+    assert abs(series - extrap) < 2e-6, (series, extrap)
+    assert abs(series - 0.0736713) < 1e-6
+    # off-centre value and symmetry
+    assert orc.torsion_exit_time(0.25, 0.5) == pytest.approx(orc.torsion_exit_time(0.5, 0.25))
+    assert orc.torsion_exit_time(0.0, 0.3) == pytest.approx(0.0, abs=1e-15)
