@@ -333,6 +333,94 @@ def run_native(args):
     return 0
 
 
+def run_batched(args):
+    """Batched uneven meshes (256 meshes, n in {65..513}, splits 2..8, one
+    bump each, 2e4 paths, dt = 5e-5): one C-ABI batch per step, replayed as a
+    CUDA graph.  Prints one JSON line (path-steps/s and meshes/s)."""
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    torch.cuda.set_device(0)
+    specs = W.config3(count=args.count)
+    if args.paths:
+        specs = [W.MeshSpec(**{**sp.__dict__, "paths": args.paths}) for sp in specs]
+    plans = [N.Plan(sp) for sp in specs]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    batch = N.Batch(plans)
+    t_create = time.perf_counter() - t0
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        batch.run(use_graph=True, stream=stream)
+    stream.synchronize()
+    steps = 0
+    solve_ok = 0
+    for i in range(len(plans)):
+        ms, ss = batch.stats(i, allow_not_converged=True)
+        steps += int(ms.path_steps)
+        solve_ok += int(ss.converged == ss.subdomains)
+    sampler = ClockSampler(0)
+    launches0 = N.sdd_kernel_launches()
+    torch.cuda.synchronize()
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            batch.run(use_graph=True, stream=stream)
+            evs[k][1].record(stream)
+            flush.zero_()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_steps = [a.elapsed_time(b) for a, b in evs]
+    t = sum(ms_steps) / 1000.0
+    nodes = sum(p.n_nodes for p in plans)
+    line = {"metric": "SDE path-steps/s", "value": steps * args.steps / t, "unit": "path-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-step/f64-acc", "data": "synthetic",
+            "config": {"workload": "batched uneven: %d meshes, n in {65,129,257,513}, splits 2..8, "
+                                   "1 bump, N=%d, dt=5e-5" % (len(plans), specs[0].paths),
+                       "interface_nodes": nodes, "path_steps_per_batch": steps,
+                       "l2": "flushed between timed steps", "graph": True},
+            "meshes_per_s": len(plans) * args.steps / t, "solves_converged": solve_ok,
+            "batch_create_s": t_create, "clocks": clocks,
+            "gpu_launches": int(N.sdd_kernel_launches() - launches0)}
+    batch.close()
+    for p in plans:
+        p.close()
+    print(json.dumps(line))
+    return 0
+
+
+def run_serve(args):
+    """Serving: Poisson stream of mesh requests (n log-uniform 65..n_max,
+    splits 2..8, 1-3 bumps), paths per node chosen by a pilot for std-err
+    <= 1e-3, continuous batching; p50/p99 latency and meshes/s."""
+    import torch
+    from paper_1310_3435_gb300 import serving as S
+    torch.cuda.set_device(0)
+    out = []
+    for rate in args.rates:
+        arr = W.config5(count=args.count, rate=rate, seed=0, n_max=args.n_max)
+        reqs = [S.Request(i, a.spec, a.arrival) for i, a in enumerate(arr)]
+        srv = S.Server(hbm_budget=150e9, n_streams=3, max_batch=args.max_batch,
+                       target_stderr=args.target_stderr)
+        t0 = time.perf_counter()
+        res = srv.run(reqs)
+        wall = time.perf_counter() - t0
+        summ = S.summarize(res)
+        summ.update({"rate_req_s": rate, "wall_s": wall, "batches_launched": srv.launches,
+                     "peak_budget_bytes": srv.peak_used})
+        out.append(summ)
+    print(json.dumps({"metric": "served latency and meshes/s", "unit": "s",
+                      "workload": "Poisson stream, n log-uniform 65..%d, splits 2..8, 1-3 bumps, "
+                                  "std-err <= %g (pilot 1024 paths), dt=5e-5"
+                                  % (args.n_max, args.target_stderr),
+                      "requests_per_rate": args.count, "results": out}))
+    return 0
+
+
 def achieved_steps_per_s(path_steps, seconds):
     return path_steps / seconds
 
@@ -367,7 +455,14 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--config", default="config2", choices=["config1", "config2", "config4"])
+    ap.add_argument("--config", default="config2",
+                    choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("--count", type=int, default=256, help="meshes (config3) or requests (--serve)")
+    ap.add_argument("--serve", action="store_true", help="serving run (config 5) instead")
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
+    ap.add_argument("--n-max", type=int, default=1025)
+    ap.add_argument("--target-stderr", type=float, default=1e-3)
+    ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--precision", type=int, default=None, help="0 FP64, 1 FP32 stepping")
     ap.add_argument("--ref-budget", type=float, default=15.0,
                     help="seconds of CPU work per oracle sample")
@@ -382,6 +477,10 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
+    if args.config == "config3":
+        return run_batched(args)
     return run_native(args)
 
 

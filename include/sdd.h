@@ -189,7 +189,9 @@ int sdd_interface_mc(sdd_plan* plan, const sdd_mc_params* mc, double* mean, doub
 int sdd_interface_mc_sums(sdd_plan* plan, const sdd_mc_params* mc, sdd_node_sums* sums,
                           void* stream);
 
-/* Statistics of the plan's last Monte Carlo call (synchronises its stream). */
+/* Statistics of the plan's last sdd_interface_mc / _sums / sdd_mesh_generate
+ * call.  Waits for that call only (an event recorded after it), not for later
+ * work on its stream.  After a batch run use sdd_batch_plan_stats. */
 int sdd_plan_last_mc_stats(sdd_plan* plan, sdd_mc_stats* stats);
 
 /* Subdomain solves (§2.1, §3.5): the interface values `iface` ([n_nodes][2],
@@ -209,7 +211,42 @@ int sdd_mesh_generate(sdd_plan* plan, const sdd_mc_params* mc, const sdd_solve_p
                       double* mesh, double* iface_mean, double* iface_stderr,
                       sdd_mc_stats* mc_stats, sdd_solve_stats* solve_stats, void* stream);
 
-/* Frees the plan and its device buffers (synchronises its last stream). */
+/* Copies the plan's last results: mesh [n][n][2] (after a solve), interface
+ * means and standard errors [n_nodes][2] (after a Monte Carlo call or a batch
+ * run).  Each pointer may be NULL, host or device memory. */
+int sdd_plan_results(sdd_plan* plan, double* mesh, double* mean, double* stderr_, void* stream);
+
+/* ---- batches: many meshes of uneven size generated together ----
+ * The interface nodes of every plan of a batch run in one persistent path
+ * kernel per (precision, density family) group, followed by one per-node
+ * reduction per group, one Dirichlet-fill launch and one launch solving every
+ * subdomain of every mesh (§2.1: the subdomains are independent, so meshes
+ * batch the same way subdomains do).  Each plan keeps its own Philox key and
+ * work-item size, so its results are bitwise the same as when it runs alone.
+ * Results land in each plan's buffers (sdd_plan_results). */
+typedef struct sdd_batch sdd_batch;
+
+/* Builds a batch over n_plans distinct plans, with one sdd_mc_params and one
+ * sdd_solve_params per plan (host arrays).  All device records are built and
+ * copied here; the call synchronises the device.  Errors: INVALID_ARG, OOM,
+ * CUDA. */
+int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* mc,
+                     const sdd_solve_params* sp, sdd_batch** out);
+
+/* Enqueues one run of the batch on `stream` (asynchronous).  use_graph != 0:
+ * the first call captures the run into a CUDA graph, later calls replay it
+ * (needs a non-default stream). */
+int sdd_batch_run(sdd_batch* batch, int use_graph, void* stream);
+
+/* Statistics of plan `index` in the batch's last run (synchronises). */
+int sdd_batch_plan_stats(sdd_batch* batch, int index, sdd_mc_stats* mc, sdd_solve_stats* solve);
+
+/* Frees the batch (not its plans). */
+void sdd_batch_destroy(sdd_batch* batch);
+
+/* Frees the plan and its device buffers.  Memory is stream-ordered: the free
+ * is queued on the plan's last stream after its work, and the call does not
+ * synchronise.  A plan must outlive the batches that use it. */
 void sdd_plan_destroy(sdd_plan* plan);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -77,6 +77,12 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -118,7 +124,7 @@ __device__ __forceinline__ void box_muller_f32_step(uint32_t ra, uint32_t rb, fl
 {
     const float ua = uniform23(ra), ub = uniform23(rb);
     const float v = c4dt * lg2_approx(ua);                  // -4 dt ln ua > 0
-    nr = -(v * rsqrt_approx(v));
+    nr = -sqrt_approx(v);
     const float ang = TWO_PI_F * (ub - 0.5f);
     cz = cos_approx(ang);
     sz = sin_approx(ang);
@@ -816,9 +822,12 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
             const float y1s = fmaf(na, ca, as), y1t = fmaf(na, sa, at);
             dens.advance(y1s, y1t, as, at);
             const float y2s = fmaf(nb, cb, as), y2t = fmaf(nb, sb, at);
+            // one test for both steps: every coordinate inside (0,1)?
+            const float lo = fminf(fminf(y1s, y1t), fminf(y2s, y2t));
+            const float hi = fmaxf(fmaxf(y1s, y1t), fmaxf(y2s, y2t));
             const bool out1 = (y1s <= 0.f) | (y1s >= 1.f) | (y1t <= 0.f) | (y1t >= 1.f);
             const bool out2 = (y2s <= 0.f) | (y2s >= 1.f) | (y2t <= 0.f) | (y2t >= 1.f);
-            if (!(out1 | out2) && k + 2u < kmax) {
+            if ((lo > 0.f) & (hi < 1.f) && k + 2u < kmax) {
                 xs = y2s;
                 xt = y2t;
                 k += 2u;
@@ -1147,7 +1156,7 @@ int mc_grid_blocks(int precision, int fc, bool one, int* blocks, int* threads)
     SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, reinterpret_cast<const void*>(path_kernel(precision, one, fc)), MC_THREADS, 0));
     *blocks = sms * std::max(per_sm, 1);
-    *threads = MC_THREADS;
+    if (threads) *threads = MC_THREADS;
     return SDD_OK;
 }
 
@@ -1158,8 +1167,17 @@ int launch_mc(const McArgs& args, int precision, int fc, cudaStream_t stream)
     int blocks = 0, threads = 0;
     int rc = mc_grid_blocks(precision, fc, one, &blocks, &threads);
     if (rc) return rc;
+    return launch_mc_sized(args, precision, fc, blocks, stream);
+}
+
+int launch_mc_sized(const McArgs& args, int precision, int fc, int blocks, cudaStream_t stream)
+{
+    if (args.total_items == 0) return SDD_OK;
+    const bool one = args.meshes == nullptr;
+    const int threads = MC_THREADS;
     const uint64_t max_blocks = (args.total_items * 32 + threads - 1) / threads;
     if ((uint64_t)blocks > max_blocks) blocks = (int)max_blocks;
+    if (blocks < 1) blocks = 1;
     SDD_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
     path_kernel(precision, one, fc)<<<blocks, threads, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());

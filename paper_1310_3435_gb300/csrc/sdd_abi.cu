@@ -7,52 +7,13 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cstdio>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "sdd_internal.h"
-
-// ------------------------------------------------------------------ plan --
-struct sdd_plan {
-    int n = 0, sx = 0, sy = 0;
-    int device = 0;
-    sdd_density dens{};
-    int bmap_mode = 0;
-    std::vector<int> ix, iy;               // interface lines
-    std::vector<int32_t> h_nodes;          // [n_nodes][2] (i, j)
-    std::vector<double> h_edges;           // [2][4][n]
-    std::vector<sdd::SubDev> h_subs;
-    int64_t n_nodes = 0;
-
-    int2* d_nodes = nullptr;
-    double* d_edges = nullptr;
-
-    // Monte Carlo
-    unsigned long long* d_queue = nullptr;
-    sdd::Slot* d_slots = nullptr;
-    uint64_t slots_cap = 0;
-    sdd_node_sums* d_sums = nullptr;
-    double* d_mean = nullptr;
-    double* d_stderr = nullptr;
-    sdd::McStatsDev* d_stats = nullptr;
-    uint64_t last_paths = 0;
-    bool have_mc = false;
-
-    // subdomain solves
-    double* d_u = nullptr;
-    double* d_cx = nullptr;
-    double* d_cy = nullptr;
-    float* d_cxf = nullptr;
-    float* d_cyf = nullptr;
-    float* d_work = nullptr;
-    sdd::SubDev* d_subs = nullptr;
-    sdd::SubStat* d_substats = nullptr;
-    bool coefs_ready = false;
-
-    cudaStream_t last_stream = nullptr;
-};
 
 namespace sdd {
 
@@ -94,19 +55,46 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync from the
+// device's default pool), so creating and destroying plans and batches never
+// synchronises the device: work already queued on other streams keeps
+// running.  Allocations go to the stream named by an AllocOn guard (the
+// call's stream, or the library's set-up stream).
+thread_local cudaStream_t t_alloc_stream = nullptr;
+
+struct AllocOn {
+    cudaStream_t prev;
+    explicit AllocOn(cudaStream_t s) : prev(t_alloc_stream) { t_alloc_stream = s; }
+    ~AllocOn() { t_alloc_stream = prev; }
+};
+
+// Library stream for set-up work (plan tables, batch records), one per
+// device, non-blocking so that it never waits for the caller's streams.
+cudaStream_t setup_stream()
+{
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
-    SDD_CUDA(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+    SDD_CUDA(cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), t_alloc_stream));
     return SDD_OK;
 }
 
 template <typename T>
-void dev_free(T*& p)
+void dev_free(T*& p, cudaStream_t s)
 {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
 }
 
@@ -187,8 +175,9 @@ int check_device(const sdd_plan* p)
     return SDD_OK;
 }
 
-int ensure_mc_buffers(sdd_plan* p, uint64_t items)
+int ensure_mc_buffers(sdd_plan* p, uint64_t items, cudaStream_t stream)
 {
+    AllocOn on(stream);
     if (!p->d_sums) {
         int rc;
         if ((rc = dev_alloc(&p->d_sums, (size_t)p->n_nodes))) return rc;
@@ -198,7 +187,7 @@ int ensure_mc_buffers(sdd_plan* p, uint64_t items)
         if ((rc = dev_alloc(&p->d_queue, 1))) return rc;
     }
     if (items > p->slots_cap) {
-        dev_free(p->d_slots);
+        dev_free(p->d_slots, stream);
         p->slots_cap = 0;
         int rc = dev_alloc(&p->d_slots, (size_t)items);
         if (rc) return rc;
@@ -207,30 +196,43 @@ int ensure_mc_buffers(sdd_plan* p, uint64_t items)
     return SDD_OK;
 }
 
+// Solve buffers of a plan: allocation and the subdomain list only (no kernel),
+// so that set-up never waits behind work running on the device.
+int alloc_solve_buffers(sdd_plan* p, cudaStream_t stream)
+{
+    if (p->d_u) return SDD_OK;
+    AllocOn on(stream);
+    const int64_t nn = (int64_t)p->n * p->n;
+    int rc;
+    if ((rc = dev_alloc(&p->d_u, (size_t)nn * 2))) return rc;
+    if ((rc = dev_alloc(&p->d_cx, (size_t)p->n * (p->n - 1)))) return rc;
+    if ((rc = dev_alloc(&p->d_cy, (size_t)p->n * (p->n - 1)))) return rc;
+    if ((rc = dev_alloc(&p->d_cxf, (size_t)p->n * (p->n - 1)))) return rc;
+    if ((rc = dev_alloc(&p->d_cyf, (size_t)p->n * (p->n - 1)))) return rc;
+    if ((rc = dev_alloc(&p->d_work, (size_t)nn * 9))) return rc;   // written before read
+    if ((rc = dev_alloc(&p->d_subs, p->h_subs.size()))) return rc;
+    if ((rc = dev_alloc(&p->d_substats, p->h_subs.size()))) return rc;
+    SDD_CUDA(cudaMemcpyAsync(p->d_subs, p->h_subs.data(), p->h_subs.size() * sizeof(SubDev),
+                             cudaMemcpyHostToDevice, stream));
+    return SDD_OK;
+}
+
+// Edge coefficients of a plan, computed once, on the stream of its first solve.
+int ensure_coefs(sdd_plan* p, cudaStream_t stream)
+{
+    if (p->coefs_ready) return SDD_OK;
+    int rc = launch_edge_coefs(p->n, p->dens.family, p->dens.coef_mode, p->dens.params, p->d_cx,
+                               p->d_cy, p->d_cxf, p->d_cyf, stream);
+    if (rc) return rc;
+    p->coefs_ready = true;
+    return SDD_OK;
+}
+
 int ensure_solve_buffers(sdd_plan* p, cudaStream_t stream)
 {
-    const int64_t nn = (int64_t)p->n * p->n;
-    if (!p->d_u) {
-        int rc;
-        if ((rc = dev_alloc(&p->d_u, (size_t)nn * 2))) return rc;
-        if ((rc = dev_alloc(&p->d_cx, (size_t)p->n * (p->n - 1)))) return rc;
-        if ((rc = dev_alloc(&p->d_cy, (size_t)p->n * (p->n - 1)))) return rc;
-        if ((rc = dev_alloc(&p->d_cxf, (size_t)p->n * (p->n - 1)))) return rc;
-        if ((rc = dev_alloc(&p->d_cyf, (size_t)p->n * (p->n - 1)))) return rc;
-        if ((rc = dev_alloc(&p->d_work, (size_t)nn * 9))) return rc;
-        if ((rc = dev_alloc(&p->d_subs, p->h_subs.size()))) return rc;
-        if ((rc = dev_alloc(&p->d_substats, p->h_subs.size()))) return rc;
-        SDD_CUDA(cudaMemcpy(p->d_subs, p->h_subs.data(), p->h_subs.size() * sizeof(SubDev),
-                            cudaMemcpyHostToDevice));
-        SDD_CUDA(cudaMemsetAsync(p->d_work, 0, (size_t)nn * 9 * sizeof(float), stream));
-    }
-    if (!p->coefs_ready) {
-        int rc = launch_edge_coefs(p->n, p->dens.family, p->dens.coef_mode, p->dens.params,
-                                   p->d_cx, p->d_cy, p->d_cxf, p->d_cyf, stream);
-        if (rc) return rc;
-        p->coefs_ready = true;
-    }
-    return SDD_OK;
+    int rc = alloc_solve_buffers(p, stream);
+    if (rc) return rc;
+    return ensure_coefs(p, stream);
 }
 
 // Paths per work item: enough items to spread over every warp slot of the
@@ -267,20 +269,17 @@ int validate_mc(const sdd_mc_params* mc)
     return SDD_OK;
 }
 
-// Builds the mesh record and launches the path kernel + reduction.
-int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stderr_dev,
-           sdd_node_sums* sums_dev, cudaStream_t stream)
+uint32_t chunk_of(const sdd_plan* p, const sdd_mc_params* mc)
 {
-    int rc = validate_mc(mc);
-    if (rc) return rc;
-    const uint32_t chunk = mc->chunk ? (uint32_t)mc->chunk : auto_chunk(mc->paths_per_node, p->n_nodes);
-    const uint32_t cpn = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
-    const uint64_t items = (uint64_t)p->n_nodes * cpn;
-    if ((rc = ensure_mc_buffers(p, items))) return rc;
+    return mc->chunk ? (uint32_t)mc->chunk : auto_chunk(mc->paths_per_node, p->n_nodes);
+}
 
-    McArgs a;
-    memset(&a, 0, sizeof(a));
-    MeshDev& m = a.single;
+// Mesh record of plan p for Monte Carlo parameters mc (outputs and offsets
+// are set by the caller).
+void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
+{
+    memset(&m, 0, sizeof(m));
+    const uint32_t chunk = chunk_of(p, mc);
     m.n = p->n;
     m.family = p->dens.family;
     m.precision = mc->precision;
@@ -288,21 +287,35 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     m.key1 = (uint32_t)(mc->seed >> 32);
     m.paths = (uint32_t)mc->paths_per_node;
     m.chunk = chunk;
-    m.chunks_per_node = cpn;
+    m.chunks_per_node = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
     m.max_steps = (uint32_t)(mc->max_steps ? mc->max_steps : (uint64_t)std::ceil(2.0 / mc->dt));
     m.n_nodes = p->n_nodes;
-    m.item_begin = 0;
-    m.node_begin = 0;
     m.dt = mc->dt;
     m.sqrt2dt = std::sqrt(2.0 * mc->dt);
     m.tie_delta = mc->tie_delta >= 0.0 ? mc->tie_delta : (mc->precision == SDD_FP64 ? 1e-11 : 0.0);
+    m.nodes = p->d_nodes;
+    m.edges = p->d_edges;
+    fill_fp32_params(m, p->dens);
+}
+
+// Builds the mesh record and launches the path kernel + reduction.
+int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stderr_dev,
+           sdd_node_sums* sums_dev, cudaStream_t stream)
+{
+    int rc = validate_mc(mc);
+    if (rc) return rc;
+    McArgs a;
+    memset(&a, 0, sizeof(a));
+    MeshDev& m = a.single;
+    mesh_record(p, mc, m);
+    const uint64_t items = (uint64_t)p->n_nodes * m.chunks_per_node;
+    if ((rc = ensure_mc_buffers(p, items, stream))) return rc;
     m.nodes = p->d_nodes;
     m.edges = p->d_edges;
     m.sums = sums_dev ? sums_dev : p->d_sums;
     m.mean = mean_dev ? mean_dev : p->d_mean;
     m.stderr_ = stderr_dev ? stderr_dev : p->d_stderr;
     m.stats = p->d_stats;
-    fill_fp32_params(m, p->dens);
     for (int r = 0; r < 10; ++r) {
         a.rk[2 * r] = m.key0 + (uint32_t)r * 0x9E3779B9u;
         a.rk[2 * r + 1] = m.key1 + (uint32_t)r * 0xBB67AE85u;
@@ -315,18 +328,17 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     a.slots = p->d_slots;
     SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
     if ((rc = launch_mc(a, mc->precision, mesh_fam_class(m.family, m.nb), stream))) return rc;
+    if (!p->mc_done) SDD_CUDA(cudaEventCreateWithFlags(&p->mc_done, cudaEventDisableTiming));
+    SDD_CUDA(cudaEventRecord(p->mc_done, stream));
     p->last_paths = mc->paths_per_node;
     p->have_mc = true;
     p->last_stream = stream;
     return SDD_OK;
 }
 
-int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
+int stats_from_dev(const McStatsDev& s, uint64_t paths, sdd_mc_stats* out)
 {
-    McStatsDev s;
-    SDD_CUDA(cudaMemcpyAsync(&s, p->d_stats, sizeof(s), cudaMemcpyDeviceToHost, stream));
-    SDD_CUDA(cudaStreamSynchronize(stream));
-    out->paths = p->last_paths * (uint64_t)p->n_nodes;
+    out->paths = paths;
     out->path_steps = s.steps;
     out->ties = s.ties;
     out->non_exits = s.caps;
@@ -336,6 +348,14 @@ int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
     if (s.lost != 0)
         return fail(SDD_ERR_CUDA, "internal error: a node's path count differs from N");
     return SDD_OK;
+}
+
+int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
+{
+    McStatsDev s;
+    SDD_CUDA(cudaMemcpyAsync(&s, p->d_stats, sizeof(s), cudaMemcpyDeviceToHost, stream));
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    return stats_from_dev(s, p->last_paths * (uint64_t)p->n_nodes, out);
 }
 
 int validate_solve(const sdd_solve_params* sp)
@@ -405,6 +425,94 @@ int read_solve_stats(sdd_plan* p, sdd_solve_stats* out, cudaStream_t stream)
     return out->converged == out->subdomains
                ? SDD_OK
                : fail(SDD_ERR_NOT_CONVERGED, "a subdomain did not reach the tolerance");
+}
+
+// ------------------------------------------------------------------ batch --
+// Many plans generated together: one path-kernel launch per (precision,
+// density class) group over all their interface nodes, one reduction per
+// group, one Dirichlet-fill launch and one solve launch over every subdomain
+// of every mesh.  Everything a run needs lives on the device from creation
+// on, so a run is a fixed sequence of memsets and kernel launches, which can
+// be captured once into a CUDA graph and replayed.
+struct McGroup {
+    int precision;
+    int fc;
+    int blocks;                 // persistent grid
+    McArgs args;
+};
+
+}  // namespace
+}  // namespace sdd
+
+struct sdd_batch {
+    int device = 0;
+    std::vector<sdd_plan*> plans;
+    std::vector<uint64_t> plan_paths;           // N per plan
+    std::vector<sdd::McGroup> groups;
+    std::vector<int> plan_slot;                 // plan -> index of its record in d_meshes
+    sdd::MeshDev* d_meshes = nullptr;
+    uint64_t* d_offs = nullptr;                 // item and node prefix sums of every group
+    sdd::Slot* d_slots = nullptr;
+    unsigned long long* d_queues = nullptr;     // one work counter per group
+    sdd::McStatsDev* d_stats = nullptr;         // one per plan
+    sdd::FillDev* d_fill = nullptr;
+    uint64_t* d_fill_off = nullptr;
+    uint64_t fill_total = 0;
+    sdd::SolveMeshDev* d_smesh = nullptr;
+    sdd::SubDev* d_subs = nullptr;
+    sdd::SubStat* d_substats = nullptr;
+    std::vector<int> sub_begin;                 // plan -> first subdomain
+    int n_subs = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool ran = false;
+};
+
+namespace sdd {
+namespace {
+
+void batch_free(sdd_batch* b)
+{
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    const cudaStream_t fs = b->ran ? b->last_stream : setup_stream();
+    dev_free(b->d_meshes, fs);
+    dev_free(b->d_offs, fs);
+    dev_free(b->d_slots, fs);
+    dev_free(b->d_queues, fs);
+    dev_free(b->d_stats, fs);
+    dev_free(b->d_fill, fs);
+    dev_free(b->d_fill_off, fs);
+    dev_free(b->d_smesh, fs);
+    dev_free(b->d_subs, fs);
+    dev_free(b->d_substats, fs);
+    delete b;
+}
+
+// Enqueues one whole run of the batch on `stream` (no host synchronisation,
+// no device queries: safe inside a stream capture).
+int batch_enqueue(sdd_batch* b, cudaStream_t stream)
+{
+    const size_t np = b->plans.size();
+    for (sdd_plan* p : b->plans) {                 // first run: edge coefficients
+        int rc = ensure_coefs(p, stream);
+        if (rc) return rc;
+    }
+    SDD_CUDA(cudaMemsetAsync(b->d_stats, 0, np * sizeof(McStatsDev), stream));
+    for (const McGroup& g : b->groups) {
+        int rc = launch_mc_sized(g.args, g.precision, g.fc, g.blocks, stream);
+        if (rc) return rc;
+    }
+    int rc = launch_fill_batched(b->d_fill, b->d_fill_off, (int)np, b->fill_total, stream);
+    if (rc) return rc;
+    SolveArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    sa.meshes = b->d_smesh;
+    sa.subs = b->d_subs;
+    sa.n_subs = b->n_subs;
+    sa.stats = b->d_substats;
+    return launch_solve(sa, stream);
 }
 
 }  // namespace
@@ -507,18 +615,23 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
         }
     }
 
-    if ((rc = dev_alloc(&p->d_nodes, (size_t)std::max<int64_t>(p->n_nodes, 1))) ||
-        (rc = dev_alloc(&p->d_edges, p->h_edges.size()))) {
-        sdd_plan_destroy(p);
-        return rc;
+    const cudaStream_t ss = setup_stream();
+    {
+        AllocOn on(ss);
+        if ((rc = dev_alloc(&p->d_nodes, (size_t)std::max<int64_t>(p->n_nodes, 1))) ||
+            (rc = dev_alloc(&p->d_edges, p->h_edges.size()))) {
+            sdd_plan_destroy(p);
+            return rc;
+        }
     }
     cudaError_t ce = cudaSuccess;
     if (p->n_nodes > 0)
-        ce = cudaMemcpy(p->d_nodes, p->h_nodes.data(), p->h_nodes.size() * sizeof(int32_t),
-                        cudaMemcpyHostToDevice);
+        ce = cudaMemcpyAsync(p->d_nodes, p->h_nodes.data(), p->h_nodes.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, ss);
     if (ce == cudaSuccess)
-        ce = cudaMemcpy(p->d_edges, p->h_edges.data(), p->h_edges.size() * sizeof(double),
-                        cudaMemcpyHostToDevice);
+        ce = cudaMemcpyAsync(p->d_edges, p->h_edges.data(), p->h_edges.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, ss);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(ss);
     if (ce != cudaSuccess) {
         rc = cuda_status(ce, "cudaMemcpy(plan tables)");
         sdd_plan_destroy(p);
@@ -603,7 +716,14 @@ int sdd_plan_last_mc_stats(sdd_plan* p, sdd_mc_stats* stats)
     if (!p->have_mc) return fail(SDD_ERR_INVALID_ARG, "no Monte Carlo call on this plan yet");
     int rc = check_device(p);
     if (rc) return rc;
-    return read_mc_stats(p, stats, p->last_stream);
+    if (!p->mc_done)
+        return fail(SDD_ERR_INVALID_ARG,
+                    "this plan's last Monte Carlo run was part of a batch: use sdd_batch_plan_stats");
+    // wait for this plan's last Monte Carlo call only, not for later work on its stream
+    SDD_CUDA(cudaEventSynchronize(p->mc_done));
+    McStatsDev s;
+    SDD_CUDA(cudaMemcpy(&s, p->d_stats, sizeof(s), cudaMemcpyDeviceToHost));
+    return stats_from_dev(s, p->last_paths * (uint64_t)p->n_nodes, stats);
 }
 
 int sdd_subdomain_solve(sdd_plan* p, const double* iface, const sdd_solve_params* sp, double* mesh,
@@ -618,7 +738,7 @@ int sdd_subdomain_solve(sdd_plan* p, const double* iface, const sdd_solve_params
     const size_t ibytes = (size_t)p->n_nodes * 2 * sizeof(double);
     const double* iface_dev = iface;
     if (iface && !is_device_ptr(iface)) {
-        if ((rc = ensure_mc_buffers(p, 0))) return rc;
+        if ((rc = ensure_mc_buffers(p, 0, stream))) return rc;
         SDD_CUDA(cudaMemcpyAsync(p->d_mean, iface, ibytes, cudaMemcpyHostToDevice, stream));
         iface_dev = p->d_mean;
     }
@@ -676,23 +796,25 @@ int sdd_mesh_generate(sdd_plan* p, const sdd_mc_params* mc, const sdd_solve_para
 void sdd_plan_destroy(sdd_plan* p)
 {
     if (!p) return;
-    if (p->last_stream || p->have_mc) cudaStreamSynchronize(p->last_stream);
-    dev_free(p->d_nodes);
-    dev_free(p->d_edges);
-    dev_free(p->d_queue);
-    dev_free(p->d_slots);
-    dev_free(p->d_sums);
-    dev_free(p->d_mean);
-    dev_free(p->d_stderr);
-    dev_free(p->d_stats);
-    dev_free(p->d_u);
-    dev_free(p->d_cx);
-    dev_free(p->d_cy);
-    dev_free(p->d_cxf);
-    dev_free(p->d_cyf);
-    dev_free(p->d_work);
-    dev_free(p->d_subs);
-    dev_free(p->d_substats);
+    // stream-ordered after the plan's last work; no device synchronisation
+    const cudaStream_t fs = p->have_mc || p->last_stream ? p->last_stream : setup_stream();
+    dev_free(p->d_nodes, fs);
+    dev_free(p->d_edges, fs);
+    dev_free(p->d_queue, fs);
+    dev_free(p->d_slots, fs);
+    dev_free(p->d_sums, fs);
+    dev_free(p->d_mean, fs);
+    dev_free(p->d_stderr, fs);
+    dev_free(p->d_stats, fs);
+    dev_free(p->d_u, fs);
+    dev_free(p->d_cx, fs);
+    dev_free(p->d_cy, fs);
+    dev_free(p->d_cxf, fs);
+    dev_free(p->d_cyf, fs);
+    dev_free(p->d_work, fs);
+    dev_free(p->d_subs, fs);
+    dev_free(p->d_substats, fs);
+    if (p->mc_done) cudaEventDestroy(p->mc_done);
     delete p;
 }
 
@@ -702,6 +824,299 @@ int sdd_kernel_launches(uint64_t* count)
 {
     if (!count) return fail(SDD_ERR_INVALID_ARG, "count is NULL");
     *count = g_launches.load(std::memory_order_relaxed);
+    return SDD_OK;
+}
+
+int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* mc,
+                     const sdd_solve_params* sp, sdd_batch** out)
+{
+    clear_error();
+    if (!out) return fail(SDD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!plans || !mc || !sp || n_plans <= 0)
+        return fail(SDD_ERR_INVALID_ARG, "plans, mc and sp must hold n_plans > 0 entries");
+    int rc;
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return fail(SDD_ERR_INVALID_ARG, "NULL plan in batch");
+        if ((rc = check_device(plans[i]))) return rc;
+        if ((rc = validate_mc(&mc[i]))) return rc;
+        if ((rc = validate_solve(&sp[i]))) return rc;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return fail(SDD_ERR_INVALID_ARG, "a plan appears twice in a batch");
+    }
+    sdd_batch* b = new (std::nothrow) sdd_batch();
+    if (!b) return fail(SDD_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&b->device);
+    b->plans.assign(plans, plans + n_plans);
+    b->plan_slot.assign(n_plans, -1);
+    for (int i = 0; i < n_plans; ++i) b->plan_paths.push_back(mc[i].paths_per_node);
+
+    // per-plan device buffers (outputs, solve buffers, edge coefficients) and
+    // the batch's records are set up on the library's set-up stream, which is
+    // synchronised (alone) before the batch is returned
+    const cudaStream_t ss = setup_stream();
+    AllocOn on(ss);
+    for (int i = 0; i < n_plans; ++i) {
+        if ((rc = ensure_mc_buffers(plans[i], 0, ss)) || (rc = alloc_solve_buffers(plans[i], ss))) {
+            batch_free(b);
+            return rc;
+        }
+    }
+    // group meshes by (precision, density class); records in group order
+    std::vector<std::pair<int, int>> key(n_plans);
+    for (int i = 0; i < n_plans; ++i) {
+        const int nb = plans[i]->dens.family == SDD_FAMILY_BUMPS ? (int)plans[i]->dens.params[0] : 0;
+        key[i] = {mc[i].precision, mesh_fam_class(plans[i]->dens.family, nb)};
+    }
+    std::vector<int> order(n_plans);
+    for (int i = 0; i < n_plans; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
+
+    std::vector<MeshDev> recs(n_plans);
+    std::vector<uint64_t> offs;
+    uint64_t slot_total = 0;
+    struct GInfo { int precision, fc, first, count; size_t item_off, node_off; uint64_t items, nodes, slot_base; };
+    std::vector<GInfo> gi;
+    for (int k = 0; k < n_plans;) {
+        int e = k;
+        while (e < n_plans && key[order[e]] == key[order[k]]) ++e;
+        GInfo g{key[order[k]].first, key[order[k]].second, k, e - k, 0, 0, 0, 0, slot_total};
+        g.item_off = offs.size();
+        uint64_t it = 0;
+        for (int q = k; q < e; ++q) {
+            const int i = order[q];
+            MeshDev& m = recs[q];
+            mesh_record(plans[i], &mc[i], m);
+            m.item_begin = it;
+            offs.push_back(it);
+            it += (uint64_t)plans[i]->n_nodes * m.chunks_per_node;
+            b->plan_slot[i] = q;
+        }
+        offs.push_back(it);
+        g.items = it;
+        g.node_off = offs.size();
+        uint64_t nd = 0;
+        for (int q = k; q < e; ++q) {
+            recs[q].node_begin = nd;
+            offs.push_back(nd);
+            nd += (uint64_t)plans[order[q]]->n_nodes;
+        }
+        offs.push_back(nd);
+        g.nodes = nd;
+        slot_total += it;
+        gi.push_back(g);
+        k = e;
+    }
+    // solve records, fill records, subdomain list
+    std::vector<SolveMeshDev> sm(n_plans);
+    std::vector<FillDev> fill(n_plans);
+    std::vector<uint64_t> fill_off(n_plans + 1, 0);
+    std::vector<SubDev> subs;
+    for (int i = 0; i < n_plans; ++i) {
+        sdd_plan* p = plans[i];
+        SolveMeshDev& r = sm[i];
+        memset(&r, 0, sizeof(r));
+        r.n = p->n;
+        r.solver = sp[i].solver;
+        r.max_iter = sp[i].max_iter > 0 ? sp[i].max_iter : (sp[i].solver == SDD_SOLVER_SOR ? 200000 : 20000);
+        r.tol = sp[i].tol;
+        r.omega = sp[i].omega;
+        r.u = p->d_u;
+        r.cx = p->d_cx;
+        r.cy = p->d_cy;
+        r.cxf = p->d_cxf;
+        r.cyf = p->d_cyf;
+        r.work = p->d_work;
+        FillDev& f = fill[i];
+        memset(&f, 0, sizeof(f));
+        f.n = p->n;
+        f.n_nodes = p->n_nodes;
+        f.edges = p->d_edges;
+        f.nodes = p->d_nodes;
+        f.iface = p->d_mean;
+        f.u = p->d_u;
+        fill_off[i + 1] = fill_off[i] + 4 * (uint64_t)p->n + (uint64_t)p->n_nodes;
+        b->sub_begin.push_back((int)subs.size());
+        for (SubDev d : p->h_subs) {
+            d.mesh = i;
+            subs.push_back(d);
+        }
+    }
+    b->n_subs = (int)subs.size();
+    b->fill_total = fill_off[n_plans];
+
+    const size_t ng = gi.size();
+    if ((rc = dev_alloc(&b->d_meshes, recs.size())) || (rc = dev_alloc(&b->d_offs, offs.size())) ||
+        (rc = dev_alloc(&b->d_slots, (size_t)std::max<uint64_t>(slot_total, 1))) ||
+        (rc = dev_alloc(&b->d_queues, ng)) || (rc = dev_alloc(&b->d_stats, (size_t)n_plans)) ||
+        (rc = dev_alloc(&b->d_fill, (size_t)n_plans)) ||
+        (rc = dev_alloc(&b->d_fill_off, (size_t)n_plans + 1)) ||
+        (rc = dev_alloc(&b->d_smesh, (size_t)n_plans)) ||
+        (rc = dev_alloc(&b->d_subs, std::max<size_t>(subs.size(), 1))) ||
+        (rc = dev_alloc(&b->d_substats, std::max<size_t>(subs.size(), 1)))) {
+        batch_free(b);
+        return rc;
+    }
+    // outputs of each record: the plan's own buffers; stats per plan
+    for (int i = 0; i < n_plans; ++i) {
+        MeshDev& m = recs[b->plan_slot[i]];
+        m.sums = plans[i]->d_sums;
+        m.mean = plans[i]->d_mean;
+        m.stderr_ = plans[i]->d_stderr;
+        m.stats = b->d_stats + i;
+    }
+    const auto h2d = cudaMemcpyHostToDevice;
+    cudaError_t ce = cudaMemcpyAsync(b->d_meshes, recs.data(), recs.size() * sizeof(MeshDev), h2d, ss);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_offs, offs.data(), offs.size() * sizeof(uint64_t), h2d, ss);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_fill, fill.data(), fill.size() * sizeof(FillDev), h2d, ss);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_fill_off, fill_off.data(), fill_off.size() * sizeof(uint64_t), h2d, ss);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_smesh, sm.data(), sm.size() * sizeof(SolveMeshDev), h2d, ss);
+    if (ce == cudaSuccess && !subs.empty()) ce = cudaMemcpyAsync(b->d_subs, subs.data(), subs.size() * sizeof(SubDev), h2d, ss);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(ss);
+    if (ce != cudaSuccess) {
+        rc = cuda_status(ce, "cudaMemcpy(batch records)");
+        batch_free(b);
+        return rc;
+    }
+    for (size_t k = 0; k < ng; ++k) {
+        const GInfo& g = gi[k];
+        McGroup G;
+        memset(&G, 0, sizeof(G));
+        G.precision = g.precision;
+        G.fc = g.fc;
+        if ((rc = mc_grid_blocks(g.precision, g.fc, false, &G.blocks, nullptr))) {
+            batch_free(b);
+            return rc;
+        }
+        McArgs& a = G.args;
+        a.meshes = b->d_meshes + g.first;
+        a.n_meshes = g.count;
+        a.item_off = b->d_offs + g.item_off;
+        a.node_off = b->d_offs + g.node_off;
+        a.total_items = g.items;
+        a.total_nodes = g.nodes;
+        a.queue = b->d_queues + k;
+        a.slots = b->d_slots + g.slot_base;
+        b->groups.push_back(G);
+    }
+    *out = b;
+    return SDD_OK;
+}
+
+int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
+{
+    clear_error();
+    if (!b) return fail(SDD_ERR_INVALID_ARG, "batch is NULL");
+    int dev = -1;
+    SDD_CUDA(cudaGetDevice(&dev));
+    if (dev != b->device) return fail(SDD_ERR_INVALID_ARG, "batch belongs to another device");
+    cudaStream_t stream = as_stream(stream_);
+    int rc;
+    if (use_graph) {
+        if (stream == nullptr)
+            return fail(SDD_ERR_INVALID_ARG, "a graph launch needs a non-default stream");
+        if (!b->graph_exec) {
+            SDD_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            rc = batch_enqueue(b, stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(stream, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            SDD_CUDA(ce);
+            b->graph = g;
+            SDD_CUDA(cudaGraphInstantiate(&b->graph_exec, b->graph, 0));
+        }
+        SDD_CUDA(cudaGraphLaunch(b->graph_exec, stream));
+    } else {
+        if ((rc = batch_enqueue(b, stream))) return rc;
+    }
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        sdd_plan* p = b->plans[i];
+        p->last_paths = b->plan_paths[i];
+        p->have_mc = true;
+        p->last_stream = stream;
+        if (p->mc_done) {                        // the batch's stats live in the batch
+            cudaEventDestroy(p->mc_done);
+            p->mc_done = nullptr;
+        }
+    }
+    b->last_stream = stream;
+    b->ran = true;
+    return SDD_OK;
+}
+
+int sdd_batch_plan_stats(sdd_batch* b, int index, sdd_mc_stats* mc, sdd_solve_stats* solve)
+{
+    clear_error();
+    if (!b || index < 0 || index >= (int)b->plans.size())
+        return fail(SDD_ERR_INVALID_ARG, "bad batch or index");
+    if (!b->ran) return fail(SDD_ERR_INVALID_ARG, "the batch has not run yet");
+    SDD_CUDA(cudaStreamSynchronize(b->last_stream));
+    sdd_plan* p = b->plans[index];
+    int rc = SDD_OK;
+    if (mc) {
+        McStatsDev s;
+        SDD_CUDA(cudaMemcpy(&s, b->d_stats + index, sizeof(s), cudaMemcpyDeviceToHost));
+        if ((rc = stats_from_dev(s, b->plan_paths[index] * (uint64_t)p->n_nodes, mc))) return rc;
+    }
+    if (solve) {
+        const int nsub = (int)p->h_subs.size();
+        std::vector<SubStat> st(nsub);
+        if (nsub)
+            SDD_CUDA(cudaMemcpy(st.data(), b->d_substats + b->sub_begin[index],
+                                nsub * sizeof(SubStat), cudaMemcpyDeviceToHost));
+        solve->subdomains = nsub;
+        solve->converged = 0;
+        solve->max_iterations = 0;
+        solve->max_rel_residual = 0.0;
+        for (const SubStat& x : st) {
+            solve->converged += x.converged;
+            solve->max_iterations = std::max(solve->max_iterations, x.iterations);
+            solve->max_rel_residual = std::max(solve->max_rel_residual, x.rel_residual);
+        }
+        if (solve->converged != solve->subdomains)
+            return fail(SDD_ERR_NOT_CONVERGED, "a subdomain did not reach the tolerance");
+    }
+    return SDD_OK;
+}
+
+void sdd_batch_destroy(sdd_batch* b)
+{
+    if (!b) return;
+    batch_free(b);                 // stream-ordered after the batch's last run
+}
+
+int sdd_plan_results(sdd_plan* p, double* mesh, double* mean, double* stderr_, void* stream_)
+{
+    clear_error();
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "plan is NULL");
+    int rc = check_device(p);
+    if (rc) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    bool host = false;
+    const size_t mbytes = (size_t)p->n * p->n * 2 * sizeof(double);
+    const size_t ibytes = (size_t)p->n_nodes * 2 * sizeof(double);
+    if (mesh) {
+        if (!p->d_u) return fail(SDD_ERR_INVALID_ARG, "no mesh has been generated on this plan");
+        const bool d = is_device_ptr(mesh);
+        SDD_CUDA(cudaMemcpyAsync(mesh, p->d_u, mbytes, d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        host = host || !d;
+    }
+    if ((mean || stderr_) && !p->have_mc)
+        return fail(SDD_ERR_INVALID_ARG, "no Monte Carlo call on this plan yet");
+    if (mean && ibytes) {
+        const bool d = is_device_ptr(mean);
+        SDD_CUDA(cudaMemcpyAsync(mean, p->d_mean, ibytes, d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        host = host || !d;
+    }
+    if (stderr_ && ibytes) {
+        const bool d = is_device_ptr(stderr_);
+        SDD_CUDA(cudaMemcpyAsync(stderr_, p->d_stderr, ibytes, d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        host = host || !d;
+    }
+    if (host) SDD_CUDA(cudaStreamSynchronize(stream));
     return SDD_OK;
 }
 

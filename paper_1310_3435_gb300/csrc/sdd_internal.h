@@ -103,6 +103,10 @@ constexpr int kFamAny = 6;
 // reduction.
 int launch_mc(const McArgs& args, int precision, int fc, cudaStream_t stream);
 
+// Same with a precomputed persistent-grid size (no device queries: usable
+// while a stream is being captured into a CUDA graph).
+int launch_mc_sized(const McArgs& args, int precision, int fc, int blocks, cudaStream_t stream);
+
 // Persistent-grid size of the path kernel for the current device.
 int mc_grid_blocks(int precision, int fc, bool one, int* blocks, int* threads);
 
@@ -152,4 +156,63 @@ struct SolveArgs {
 };
 int launch_solve(const SolveArgs& args, cudaStream_t stream);
 
+// Batched Dirichlet fill: boundary tables and interface values of several
+// meshes into their mesh arrays, one launch.  `off` holds the device prefix
+// sums of the per-mesh element counts 4 n + n_nodes (n_meshes + 1 entries).
+struct FillDev {
+    int32_t n;
+    int32_t reserved;
+    int64_t n_nodes;
+    const double* edges;
+    const int2* nodes;
+    const double* iface;
+    double* u;
+};
+int launch_fill_batched(const FillDev* d_fill, const uint64_t* d_off, int n_meshes,
+                        uint64_t total, cudaStream_t stream);
+
 }  // namespace sdd
+
+// ------------------------------------------------------------------ plan --
+// Plan: the request description, its host tables and its resident device
+// buffers (allocated lazily, kept across calls).
+struct sdd_plan {
+    int n = 0, sx = 0, sy = 0;
+    int device = 0;
+    sdd_density dens{};
+    int bmap_mode = 0;
+    std::vector<int> ix, iy;               // interface lines
+    std::vector<int32_t> h_nodes;          // [n_nodes][2] (i, j)
+    std::vector<double> h_edges;           // [2][4][n]
+    std::vector<sdd::SubDev> h_subs;
+    int64_t n_nodes = 0;
+
+    int2* d_nodes = nullptr;
+    double* d_edges = nullptr;
+
+    // Monte Carlo
+    unsigned long long* d_queue = nullptr;
+    sdd::Slot* d_slots = nullptr;
+    uint64_t slots_cap = 0;
+    sdd_node_sums* d_sums = nullptr;
+    double* d_mean = nullptr;
+    double* d_stderr = nullptr;
+    sdd::McStatsDev* d_stats = nullptr;
+    uint64_t last_paths = 0;
+    bool have_mc = false;
+    cudaEvent_t mc_done = nullptr;         // recorded after each single-plan Monte Carlo call
+
+    // subdomain solves
+    double* d_u = nullptr;
+    double* d_cx = nullptr;
+    double* d_cy = nullptr;
+    float* d_cxf = nullptr;
+    float* d_cyf = nullptr;
+    float* d_work = nullptr;
+    sdd::SubDev* d_subs = nullptr;
+    sdd::SubStat* d_substats = nullptr;
+    bool coefs_ready = false;
+
+    cudaStream_t last_stream = nullptr;
+};
+

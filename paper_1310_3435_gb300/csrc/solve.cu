@@ -107,6 +107,42 @@ __global__ void k_fill_ring(int n, const double* __restrict__ edges, const int2*
     }
 }
 
+// Batched form: one thread per boundary-table entry or interface node of any
+// mesh of the batch (mesh found by binary search of the prefix offsets).
+__global__ void k_fill_ring_batched(const FillDev* __restrict__ fill, const uint64_t* __restrict__ off,
+                                    int n_meshes, uint64_t total)
+{
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo = 0, hi = n_meshes;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= g) lo = mid; else hi = mid;
+    }
+    const FillDev& F = fill[lo];
+    const int64_t x = (int64_t)(g - off[lo]);
+    const int n = F.n;
+    double2* __restrict__ u = reinterpret_cast<double2*>(F.u);
+    const int64_t nb = 4 * (int64_t)n;
+    if (x < nb) {
+        const int e = (int)(x / n), k = (int)(x % n);
+        const double v0 = F.edges[(0 * 4 + e) * (int64_t)n + k];
+        const double v1 = F.edges[(1 * 4 + e) * (int64_t)n + k];
+        int64_t idx;
+        if (e == 0) idx = k;
+        else if (e == 1) idx = (int64_t)(n - 1) * n + k;
+        else {
+            if (k == 0 || k == n - 1) return;
+            idx = (int64_t)k * n + (e == 2 ? 0 : n - 1);
+        }
+        u[idx] = make_double2(v0, v1);
+    } else if (x - nb < F.n_nodes) {
+        const int64_t v = x - nb;
+        const int2 ij = F.nodes[v];
+        u[(int64_t)ij.y * n + ij.x] = make_double2(F.iface[2 * v], F.iface[2 * v + 1]);
+    }
+}
+
 // Transfinite (Coons) interpolation of each subdomain's ring as the start
 // value of its interior.
 __global__ void k_coons(SolveArgs a)
@@ -461,6 +497,17 @@ int launch_fill_mesh(int n, const double* edges, const int2* nodes, int64_t n_no
     const int64_t total = 4 * (int64_t)n + n_nodes;
     k_fill_ring<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(
         n, edges, nodes, n_nodes, iface, reinterpret_cast<double2*>(u));
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
+
+int launch_fill_batched(const FillDev* d_fill, const uint64_t* d_off, int n_meshes,
+                        uint64_t total, cudaStream_t stream)
+{
+    if (total == 0) return SDD_OK;
+    k_fill_ring_batched<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(d_fill, d_off,
+                                                                             n_meshes, total);
     SDD_CUDA(cudaGetLastError());
     count_launch();
     return SDD_OK;

@@ -137,9 +137,18 @@ def load(build_if_missing: bool = True):
     L.sdd_last_error.argtypes = []
     L.sdd_last_error.restype = ctypes.c_char_p
     L.sdd_kernel_launches.argtypes = [P(ctypes.c_uint64)]
+    L.sdd_plan_results.argtypes = [vp, vp, vp, vp, vp]
+    L.sdd_batch_create.argtypes = [P(vp), ctypes.c_int, P(sdd_mc_params), P(sdd_solve_params),
+                                   P(vp)]
+    L.sdd_batch_run.argtypes = [vp, ctypes.c_int, vp]
+    L.sdd_batch_plan_stats.argtypes = [vp, ctypes.c_int, P(sdd_mc_stats), P(sdd_solve_stats)]
+    L.sdd_batch_destroy.argtypes = [vp]
+    L.sdd_batch_destroy.restype = None
     for name in ("sdd_mesh_plan", "sdd_plan_num_nodes", "sdd_plan_nodes", "sdd_plan_edges",
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
-                 "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches"):
+                 "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
+                 "sdd_plan_results", "sdd_batch_create", "sdd_batch_run",
+                 "sdd_batch_plan_stats"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -297,6 +306,41 @@ def sdd_mesh_generate(plan, mc: sdd_mc_params, sp: sdd_solve_params, mesh, iface
     return (ms, ss) if want_stats else None
 
 
+def sdd_plan_results(plan, mesh=None, mean=None, stderr=None, stream=None) -> None:
+    _check(load().sdd_plan_results(plan, _ptr(mesh), _ptr(mean), _ptr(stderr), _stream(stream)),
+           "sdd_plan_results")
+
+
+def sdd_batch_create(plans, mcs, sps):
+    """plans: sequence of plan handles; mcs / sps: one parameter record each."""
+    n = len(plans)
+    if not (len(mcs) == len(sps) == n):
+        raise ValueError("one mc and one solve record per plan")
+    ph = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    ma = (sdd_mc_params * n)(*mcs)
+    sa = (sdd_solve_params * n)(*sps)
+    h = ctypes.c_void_p()
+    _check(load().sdd_batch_create(ph, n, ma, sa, ctypes.byref(h)), "sdd_batch_create")
+    return h
+
+
+def sdd_batch_run(batch, use_graph: bool = False, stream=None) -> None:
+    _check(load().sdd_batch_run(batch, 1 if use_graph else 0, _stream(stream)), "sdd_batch_run")
+
+
+def sdd_batch_plan_stats(batch, index: int, allow_not_converged: bool = False):
+    ms, ss = sdd_mc_stats(), sdd_solve_stats()
+    allow = (SDD_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    _check(load().sdd_batch_plan_stats(batch, int(index), ctypes.byref(ms), ctypes.byref(ss)),
+           "sdd_batch_plan_stats", allow)
+    return ms, ss
+
+
+def sdd_batch_destroy(batch) -> None:
+    if batch:
+        load().sdd_batch_destroy(batch)
+
+
 def sdd_plan_destroy(plan) -> None:
     if plan:
         load().sdd_plan_destroy(plan)
@@ -349,6 +393,39 @@ class Plan:
     def close(self):
         if self.handle:
             sdd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Owning wrapper of a batch over `Plan` objects (which it keeps alive)."""
+
+    def __init__(self, plans, mcs=None, sps=None):
+        self.plans = list(plans)
+        mcs = mcs or [p.mc_params() for p in self.plans]
+        sps = sps or [p.solve_params() for p in self.plans]
+        self.handle = sdd_batch_create([p.handle for p in self.plans], mcs, sps)
+
+    def run(self, use_graph: bool = False, stream=None) -> None:
+        sdd_batch_run(self.handle, use_graph, stream)
+
+    def stats(self, index: int, allow_not_converged: bool = False):
+        return sdd_batch_plan_stats(self.handle, index, allow_not_converged)
+
+    def close(self):
+        if self.handle:
+            sdd_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,241 @@
+"""Continuous-batching server for mesh-generation requests.
+
+Requests (grid size, subdomain split, density, boundary map, time step, seed)
+arrive over time.  The server admits them while their device memory fits an
+HBM budget. Each admitted request may get a pilot Monte Carlo run that picks
+its paths per node for a target standard error. Admitted requests are grouped
+into batches, one C-ABI batch each (one path launch per density family, one
+solve launch). Up to `n_streams` batches are in flight at once on separate
+CUDA streams, so a batch formed from requests that arrived while another was
+running starts as soon as SMs free up, and their work overlaps on the
+device. Completed batches are polled through CUDA events. Their plans are
+released stream-ordered, and the memory budget is handed back.
+
+Every request keeps its own Philox key and work-item size, so its result is
+bitwise the same alone and in any mix (see tests/test_gpu_serving.py).
+PyTorch is used for streams, events and pinned host buffers only.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+from . import native as N
+
+SLOT_BYTES = 144            # device bytes of one work-item slot
+
+
+@dataclass
+class Request:
+    rid: int
+    spec: object                 # attributes as workloads.MeshSpec
+    arrival: float = 0.0         # seconds after the server starts
+
+
+@dataclass
+class Result:
+    rid: int
+    spec: object
+    paths: int
+    mesh: np.ndarray
+    mean: np.ndarray
+    stderr: np.ndarray
+    path_steps: int
+    max_stderr: float
+    arrival: float
+    admitted: float
+    started: float
+    done: float
+    batch: int
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def auto_chunk_host(paths: int, n_nodes: int, sms: int) -> int:
+    """Mirror of the library's automatic work-item size (for memory estimates)."""
+    target = paths * n_nodes / (32.0 * 24.0 * sms)
+    c = 64
+    while c < 4096 and 2 * c <= target:
+        c *= 2
+    return min(c, ((paths + 31) // 32) * 32)
+
+
+def device_bytes(n: int, n_nodes: int, paths: int, sms: int = 152) -> int:
+    """Device memory of one request's plan: tables, work-item slots, node
+    outputs, mesh, edge coefficients (FP64 + FP32) and the CG workspace."""
+    chunk = auto_chunk_host(paths, max(n_nodes, 1), sms)
+    items = n_nodes * ((paths + chunk - 1) // chunk)
+    return (8 * n_nodes + 64 * n + items * SLOT_BYTES + n_nodes * (96 + 32)
+            + 16 * n * n + 24 * n * (n - 1) + 36 * n * n + 4096)
+
+
+@dataclass
+class _InFlight:
+    bid: int
+    batch: object
+    reqs: list
+    plans: list
+    paths: list
+    stream: object
+    event: object
+    started: float
+    nbytes: int
+
+
+class Server:
+    """Admission by memory budget, pilot-chosen paths, continuous batching.
+
+    Request states: arrived -> admitted (plan built, pilot Monte Carlo queued
+    on the pilot stream) -> ready (paths per node chosen) -> in a batch on one
+    of the batch streams -> done.  The host never waits for the device: pilots
+    and batches are polled through CUDA events."""
+
+    def __init__(self, hbm_budget: float = 150e9, n_streams: int = 3, max_batch: int = 256,
+                 target_stderr: float | None = 1e-3, pilot_paths: int = 1024,
+                 min_paths: int = 1024, max_paths: int = 4_000_000, use_graph: bool = False):
+        import torch
+        self.torch = torch
+        self.budget = float(hbm_budget)
+        self.n_streams = n_streams
+        self.max_batch = max_batch
+        self.target = target_stderr
+        self.pilot_paths = pilot_paths
+        self.min_paths = min_paths
+        self.max_paths = max_paths
+        self.use_graph = use_graph
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.pilot_stream = torch.cuda.Stream()
+        self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.used = 0
+        self.peak_used = 0
+        self.launches = 0
+
+    def _paths_for(self, spec, pilot_stats) -> int:
+        """N = ceil((sigma_max / target)^2) with sigma = pilot stderr sqrt(N_pilot)."""
+        if not self.target:
+            return int(spec.paths)
+        sigma = pilot_stats.max_stderr * math.sqrt(self.pilot_paths)
+        need = int(math.ceil((sigma / self.target) ** 2))
+        return int(min(self.max_paths, max(self.min_paths, need)))
+
+    def run(self, requests, time_scale: float = 1.0, poll_sleep: float = 0.0002):
+        """Serves `requests` in real time (arrival times in seconds, divided by
+        time_scale); returns the results in completion order."""
+        torch = self.torch
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        piloting = deque()            # [req, plan, event, base_bytes, t_admit]
+        ready = deque()               # [req, plan, paths, nbytes, t_admit]
+        inflight: list[_InFlight] = []
+        results = []
+        free_streams = deque(range(self.n_streams))
+        bid = 0
+        t0 = time.perf_counter()
+        now = lambda: (time.perf_counter() - t0) * time_scale
+        while pending or piloting or ready or inflight:
+            progressed = False
+            t = now()
+            # 1. admission (FIFO) while the request's base memory fits the budget
+            while pending and pending[0].arrival <= t:
+                req = pending[0]
+                base = device_bytes(req.spec.n, req.spec.n_interface_nodes(),
+                                    self.pilot_paths if self.target else int(req.spec.paths),
+                                    self.sms)
+                if self.used + base > self.budget and (piloting or ready or inflight):
+                    break                                   # wait for memory to free up
+                pending.popleft()
+                plan = N.Plan(req.spec)
+                self.used += base
+                self.peak_used = max(self.peak_used, self.used)
+                ev = None
+                if self.target:
+                    N.sdd_interface_mc(plan.handle, plan.mc_params(paths=self.pilot_paths),
+                                       want_stats=False, stream=self.pilot_stream)
+                    ev = torch.cuda.Event()
+                    ev.record(self.pilot_stream)
+                piloting.append([req, plan, ev, base, now()])
+                progressed = True
+            # 2. pilots done -> paths per node chosen, memory re-estimated
+            while piloting and (piloting[0][2] is None or piloting[0][2].query()):
+                req, plan, ev, base, ta = piloting.popleft()
+                st = N.sdd_plan_last_mc_stats(plan.handle) if ev is not None else None
+                paths = self._paths_for(req.spec, st)
+                nbytes = device_bytes(req.spec.n, plan.n_nodes, paths, self.sms)
+                self.used += nbytes - base
+                self.peak_used = max(self.peak_used, self.used)
+                ready.append([req, plan, paths, nbytes, ta])
+                progressed = True
+            # 3. launch everything ready as one batch on a free stream
+            if ready and free_streams:
+                take = [ready.popleft() for _ in range(min(self.max_batch, len(ready)))]
+                plans = [x[1] for x in take]
+                mcs = [p.mc_params(paths=x[2]) for p, x in zip(plans, take)]
+                batch = N.Batch(plans, mcs, [p.solve_params() for p in plans])
+                si = free_streams.popleft()
+                stream = self.streams[si]
+                started = now()
+                batch.run(use_graph=self.use_graph, stream=stream)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                inflight.append(_InFlight(bid, batch, [x[0] for x in take], plans,
+                                          [x[2] for x in take], (si, stream), ev, started,
+                                          sum(x[3] for x in take)))
+                for x in take:
+                    x[0].admitted_at = x[4]
+                bid += 1
+                self.launches += 1
+                progressed = True
+            # 4. completion
+            still = []
+            for f in inflight:
+                if f.event.query():
+                    done = now()
+                    for k, (req, plan) in enumerate(zip(f.reqs, f.plans)):
+                        n = plan.n
+                        mesh = np.empty((n, n, 2))
+                        mean = np.empty((plan.n_nodes, 2))
+                        se = np.empty((plan.n_nodes, 2))
+                        N.sdd_plan_results(plan.handle, mesh, mean, se, stream=f.stream[1])
+                        ms, _ = f.batch.stats(k, allow_not_converged=True)
+                        results.append(Result(req.rid, req.spec, f.paths[k], mesh, mean, se,
+                                              int(ms.path_steps), float(ms.max_stderr),
+                                              req.arrival, getattr(req, "admitted_at", f.started),
+                                              f.started, done, f.bid))
+                    f.batch.close()
+                    for plan in f.plans:
+                        plan.close()
+                    self.used -= f.nbytes
+                    free_streams.append(f.stream[0])
+                    progressed = True
+                else:
+                    still.append(f)
+            inflight = still
+            if not progressed:
+                if pending and not (piloting or ready or inflight):
+                    wait = (pending[0].arrival - now()) / time_scale
+                    if wait > 0:
+                        time.sleep(min(wait, 0.05))
+                else:
+                    time.sleep(poll_sleep)
+        return results
+
+
+def summarize(results, wall: float | None = None) -> dict:
+    """p50 / p99 latency, meshes/s and path-steps/s of a served run."""
+    if not results:
+        return {"requests": 0}
+    lat = np.array([r.latency for r in results])
+    t_first = min(r.arrival for r in results)
+    t_last = max(r.done for r in results)
+    span = wall if wall is not None else (t_last - t_first)
+    steps = sum(r.path_steps for r in results)
+    return {"requests": len(results), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "meshes_per_s": len(results) / span, "path_steps_per_s": steps / span,
+            "span_s": span, "max_stderr": float(max(r.max_stderr for r in results)),
+            "batches": len({r.batch for r in results})}

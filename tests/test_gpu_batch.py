@@ -1,0 +1,87 @@
+"""Batched generation of uneven meshes (one path launch per density class,
+one solve launch for every subdomain), with and without CUDA-graph replay:
+every mesh's results are bitwise the same as when it runs alone."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import gpu_plan
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    specs = W.config3(count=5, seed=3, paths=640, dt=2e-4)
+    specs += [
+        W.config1(paths=512, precision=W.FP64),
+        W.MeshSpec(n=41, sx=3, sy=2, family=W.FAMILY_RING, params=(10.0, 0.5, 0.5, 50.0, 0.25),
+                   paths=700, dt=1e-4, seed=9, precision=W.FP32_STEP,
+                   solver=W.SOLVER_CG_FP32_REFINE),
+        W.MeshSpec(n=37, sx=2, sy=4, family=W.FAMILY_RIDGE, params=(20.0, 200.0, 0.3, 0.2, 1.0),
+                   paths=333, dt=1e-4, seed=4, precision=W.FP32_STEP, coef_mode=W.COEF_INV_W),
+        W.MeshSpec(n=29, sx=2, sy=2, family=W.FAMILY_BUMPS,
+                   params=W.bumps((8.0, 0.3, 0.6, 30.0, 10.0), (3.0, 0.7, 0.2, 80.0, 80.0),
+                                  (2.0, 0.5, 0.5, 20.0, 20.0), (1.0, 0.2, 0.8, 40.0, 40.0)),
+                   paths=400, dt=1e-4, seed=5, precision=W.FP32_STEP),
+    ]
+    return specs
+
+
+def _alone(spec):
+    from paper_1310_3435_gb300 import native as N
+    with gpu_plan(spec) as P:
+        mesh = np.zeros((spec.n, spec.n, 2))
+        mean = np.zeros((P.n_nodes, 2))
+        se = np.zeros((P.n_nodes, 2))
+        ms, ss = N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), mesh, mean, se)
+        return mesh, mean, se, ms
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_alone(use_graph):
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    specs = _mix()
+    alone = [_alone(s) for s in specs]
+    plans = [gpu_plan(s) for s in specs]
+    stream = torch.cuda.Stream()
+    with N.Batch(plans) as B:
+        for rep in range(2):                       # second run replays the graph
+            B.run(use_graph=use_graph, stream=stream)
+            stream.synchronize()
+            for i, (spec, P) in enumerate(zip(specs, plans)):
+                mesh = np.zeros((spec.n, spec.n, 2))
+                mean = np.zeros((P.n_nodes, 2))
+                se = np.zeros((P.n_nodes, 2))
+                N.sdd_plan_results(P.handle, mesh, mean, se)
+                am, amean, ase, ams = alone[i]
+                assert np.array_equal(mean, amean), (i, spec.label)
+                assert np.array_equal(se, ase), (i, spec.label)
+                assert np.array_equal(mesh, am), (i, spec.label)
+                ms, ss = B.stats(i)
+                assert ms.path_steps == ams.path_steps and ms.paths == ams.paths
+                assert ss.converged == ss.subdomains
+    for P in plans:
+        P.close()
+
+
+def test_batch_launch_count_and_validation():
+    from paper_1310_3435_gb300 import native as N
+    import torch
+    specs = W.config3(count=4, seed=1, paths=256, dt=2e-4)
+    plans = [gpu_plan(s) for s in specs]
+    with N.Batch(plans) as B:
+        stream = torch.cuda.Stream()
+        before = N.sdd_kernel_launches()
+        B.run(stream=stream)
+        stream.synchronize()
+        # one density class (one bump, FP32): path + reduce, fill, coons + solve
+        assert N.sdd_kernel_launches() - before == 5
+    with pytest.raises(N.SddError):
+        N.sdd_batch_create([plans[0].handle, plans[0].handle], [plans[0].mc_params()] * 2,
+                           [plans[0].solve_params()] * 2)
+    with pytest.raises(N.SddError):
+        with N.Batch(plans[:1]) as B:
+            B.run(use_graph=True, stream=None)     # graphs need a non-default stream
+    for P in plans:
+        P.close()
