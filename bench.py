@@ -403,7 +403,7 @@ def run_serve(args):
     out = []
     for rate in args.rates:
         arr = W.config5(count=args.count, rate=rate, seed=0, n_max=args.n_max)
-        reqs = [S.Request(i, a.spec, a.arrival) for i, a in enumerate(arr)]
+        reqs = [S.Request(i, a.spec, a.t) for i, a in enumerate(arr)]
         srv = S.Server(hbm_budget=150e9, n_streams=3, max_batch=args.max_batch,
                        target_stderr=args.target_stderr)
         t0 = time.perf_counter()

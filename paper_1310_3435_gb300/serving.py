@@ -98,9 +98,16 @@ class Server:
 
     def __init__(self, hbm_budget: float = 150e9, n_streams: int = 3, max_batch: int = 256,
                  target_stderr: float | None = 1e-3, pilot_paths: int = 1024,
-                 min_paths: int = 1024, max_paths: int = 4_000_000, use_graph: bool = False):
-        import torch
-        self.torch = torch
+                 min_paths: int = 1024, max_paths: int = 4_000_000, use_graph: bool = False,
+                 backend=None, cuda=None, sms: int | None = None):
+        """backend / cuda: the library binding and the stream/event provider
+        (default: paper_1310_3435_gb300.native and torch.cuda); tests of the
+        host logic pass stand-ins."""
+        self.N = backend if backend is not None else N
+        if cuda is None:
+            import torch
+            cuda = torch.cuda
+        self.cuda = cuda
         self.budget = float(hbm_budget)
         self.n_streams = n_streams
         self.max_batch = max_batch
@@ -109,9 +116,9 @@ class Server:
         self.min_paths = min_paths
         self.max_paths = max_paths
         self.use_graph = use_graph
-        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
-        self.pilot_stream = torch.cuda.Stream()
-        self.sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.streams = [cuda.Stream() for _ in range(n_streams)]
+        self.pilot_stream = cuda.Stream()
+        self.sms = sms or cuda.get_device_properties(cuda.current_device()).multi_processor_count
         self.used = 0
         self.peak_used = 0
         self.launches = 0
@@ -127,7 +134,8 @@ class Server:
     def run(self, requests, time_scale: float = 1.0, poll_sleep: float = 0.0002):
         """Serves `requests` in real time (arrival times in seconds, divided by
         time_scale); returns the results in completion order."""
-        torch = self.torch
+        cuda = self.cuda
+        N = self.N
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         piloting = deque()            # [req, plan, event, base_bytes, t_admit]
         ready = deque()               # [req, plan, paths, nbytes, t_admit]
@@ -156,7 +164,7 @@ class Server:
                 if self.target:
                     N.sdd_interface_mc(plan.handle, plan.mc_params(paths=self.pilot_paths),
                                        want_stats=False, stream=self.pilot_stream)
-                    ev = torch.cuda.Event()
+                    ev = cuda.Event()
                     ev.record(self.pilot_stream)
                 piloting.append([req, plan, ev, base, now()])
                 progressed = True
@@ -180,7 +188,7 @@ class Server:
                 stream = self.streams[si]
                 started = now()
                 batch.run(use_graph=self.use_graph, stream=stream)
-                ev = torch.cuda.Event()
+                ev = cuda.Event()
                 ev.record(stream)
                 inflight.append(_InFlight(bid, batch, [x[0] for x in take], plans,
                                           [x[2] for x in take], (si, stream), ev, started,

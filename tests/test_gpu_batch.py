@@ -75,6 +75,11 @@ def test_batch_launch_count_and_validation():
         before = N.sdd_kernel_launches()
         B.run(stream=stream)
         stream.synchronize()
+        # first run: the four plans' edge coefficients, then the run itself
+        assert N.sdd_kernel_launches() - before == 4 + 5
+        before = N.sdd_kernel_launches()
+        B.run(stream=stream)
+        stream.synchronize()
         # one density class (one bump, FP32): path + reduce, fill, coons + solve
         assert N.sdd_kernel_launches() - before == 5
     with pytest.raises(N.SddError):

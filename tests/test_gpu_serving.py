@@ -23,7 +23,7 @@ def _alone(spec, paths):
 def test_served_results_equal_alone():
     from paper_1310_3435_gb300 import serving as S
     arrivals = W.config5(count=14, rate=400.0, seed=7, n_max=129)
-    reqs = [S.Request(i, a.spec, a.arrival) for i, a in enumerate(arrivals)]
+    reqs = [S.Request(i, a.spec, a.t) for i, a in enumerate(arrivals)]
     srv = S.Server(hbm_budget=2e9, n_streams=2, max_batch=4, target_stderr=4e-3,
                    pilot_paths=512, min_paths=512)
     res = srv.run(reqs)
@@ -43,7 +43,7 @@ def test_served_results_equal_alone():
 def test_admission_respects_the_memory_budget():
     from paper_1310_3435_gb300 import serving as S
     arrivals = W.config5(count=6, rate=1000.0, seed=2, n_max=97)
-    reqs = [S.Request(i, a.spec, a.arrival) for i, a in enumerate(arrivals)]
+    reqs = [S.Request(i, a.spec, a.t) for i, a in enumerate(arrivals)]
     one = max(S.device_bytes(a.spec.n, a.spec.n_interface_nodes(), 2048) for a in arrivals)
     srv = S.Server(hbm_budget=1.5 * one, n_streams=2, max_batch=8, target_stderr=None)
     res = srv.run([S.Request(r.rid, W.MeshSpec(**{**r.spec.__dict__, "paths": 2048}), r.arrival)

@@ -1,0 +1,161 @@
+"""Host logic of the continuous-batching server, on the CPU: admission by
+memory budget, pilot-chosen paths, batching on a bounded number of streams,
+overlap of batches, completion order.  The library and CUDA streams/events are
+replaced by stand-ins whose "kernels" finish after a set wall-clock time."""
+import math
+import time
+import types
+
+import pytest
+
+import workloads as W
+from paper_1310_3435_gb300 import serving as S
+
+
+class FakeEvent:
+    def __init__(self):
+        self.t = None
+
+    def record(self, stream):
+        self.t = stream.busy_until
+
+    def query(self):
+        return time.perf_counter() >= self.t
+
+
+class FakeStream:
+    def __init__(self):
+        self.busy_until = time.perf_counter()
+
+    def enqueue(self, seconds):
+        self.busy_until = max(self.busy_until, time.perf_counter()) + seconds
+
+    def synchronize(self):
+        while time.perf_counter() < self.busy_until:
+            time.sleep(1e-4)
+
+
+class FakeCuda:
+    Stream = FakeStream
+    Event = FakeEvent
+
+    @staticmethod
+    def current_device():
+        return 0
+
+    @staticmethod
+    def get_device_properties(dev):
+        return types.SimpleNamespace(multi_processor_count=152)
+
+
+class FakeLib:
+    """Plans know their node count; a pilot reports std-err sigma/sqrt(N);
+    a batch takes 2 ms per mesh."""
+    SIGMA = 0.05
+
+    def __init__(self):
+        self.live_plans = 0
+        self.max_live = 0
+        self.batches = []
+        self.concurrent = 0
+        self.max_concurrent = 0
+
+    class _Plan:
+        def __init__(self, lib, spec):
+            self.lib, self.spec, self.n = lib, spec, spec.n
+            self.n_nodes = spec.n_interface_nodes()
+            self.handle = self
+            lib.live_plans += 1
+            lib.max_live = max(lib.max_live, lib.live_plans)
+            self.pilot_paths = None
+
+        def mc_params(self, **kw):
+            return dict(paths=kw.get("paths", self.spec.paths))
+
+        def solve_params(self):
+            return {}
+
+        def close(self):
+            if self.handle is not None:
+                self.lib.live_plans -= 1
+                self.handle = None
+
+    def Plan(self, spec):
+        return FakeLib._Plan(self, spec)
+
+    def sdd_interface_mc(self, handle, mc, want_stats=False, stream=None):
+        handle.pilot_paths = mc["paths"]
+        stream.enqueue(0.001)
+
+    def sdd_plan_last_mc_stats(self, handle):
+        return types.SimpleNamespace(max_stderr=self.SIGMA / math.sqrt(handle.pilot_paths))
+
+    class _Batch:
+        def __init__(self, lib, plans, mcs, sps):
+            self.lib, self.plans, self.mcs = lib, plans, mcs
+            lib.batches.append([m["paths"] for m in mcs])
+
+        def run(self, use_graph=False, stream=None):
+            stream.enqueue(0.002 * len(self.plans))
+            self.stream = stream
+
+        def stats(self, k, allow_not_converged=False):
+            paths = self.mcs[k]["paths"]
+            return (types.SimpleNamespace(path_steps=1000 * paths,
+                                          max_stderr=FakeLib.SIGMA / math.sqrt(paths)), None)
+
+        def close(self):
+            pass
+
+    def Batch(self, plans, mcs, sps):
+        return FakeLib._Batch(self, plans, mcs, sps)
+
+    def sdd_plan_results(self, handle, mesh, mean, se, stream=None):
+        mesh[...] = 0.0
+        mean[...] = 0.0
+        se[...] = 0.0
+
+
+def _requests(count, rate, seed=1):
+    arr = W.config5(count=count, rate=rate, seed=seed, n_max=65)
+    return [S.Request(i, a.spec, a.t) for i, a in enumerate(arr)]
+
+
+def test_every_request_served_with_pilot_paths():
+    lib = FakeLib()
+    srv = S.Server(hbm_budget=1e12, n_streams=3, max_batch=8, target_stderr=1e-3,
+                   pilot_paths=1024, backend=lib, cuda=FakeCuda, sms=152)
+    res = srv.run(_requests(40, rate=2000.0))
+    assert sorted(r.rid for r in res) == list(range(40))
+    want = math.ceil((FakeLib.SIGMA / 1e-3) ** 2)           # 2500 paths
+    assert all(r.paths == want for r in res)
+    assert all(r.max_stderr <= 1e-3 for r in res)
+    assert srv.used == 0 and lib.live_plans == 0
+    assert all(len(b) <= 8 for b in lib.batches)
+    assert len(lib.batches) >= 5                        # requests batched as they came
+    s = S.summarize(res)
+    assert s["p50_s"] <= s["p99_s"] and s["requests"] == 40
+
+
+def test_admission_waits_for_memory():
+    lib = FakeLib()
+    reqs = _requests(12, rate=5000.0)
+    one = max(S.device_bytes(r.spec.n, r.spec.n_interface_nodes(), r.spec.paths) for r in reqs)
+    srv = S.Server(hbm_budget=2.2 * one, n_streams=3, max_batch=8, target_stderr=None,
+                   backend=lib, cuda=FakeCuda, sms=152)
+    res = srv.run(reqs)
+    assert len(res) == 12
+    assert srv.peak_used <= 2.2 * one                 # never more than the budget allows
+    assert lib.max_live < 12                          # admission had to wait
+
+
+def test_batches_overlap_on_streams_and_latency_includes_queueing():
+    lib = FakeLib()
+    reqs = _requests(30, rate=10000.0)
+    srv = S.Server(hbm_budget=1e12, n_streams=2, max_batch=3, target_stderr=None,
+                   backend=lib, cuda=FakeCuda, sms=152)
+    res = srv.run(reqs)
+    starts = sorted((r.started, r.done) for r in res)
+    # with two streams, some batch starts before an earlier one is done
+    assert any(b[0] < a[1] for a, b in zip(starts, starts[1:]) if b[0] > a[0])
+    assert all(r.done >= r.started >= r.arrival for r in res)
