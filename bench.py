@@ -375,6 +375,16 @@ def run_batched(args):
     ms_steps = [a.elapsed_time(b) for a, b in evs]
     t = sum(ms_steps) / 1000.0
     nodes = sum(p.n_nodes for p in plans)
+    # phases timed apart (no graph): interface Monte Carlo, then fill + solves
+    ph = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ph[0].record(stream)
+    batch.run_phases(1, stream=stream)
+    ph[1].record(stream)
+    batch.run_phases(2, stream=stream)
+    ph[2].record(stream)
+    torch.cuda.synchronize()
+    ms_mc, ms_solve = ph[0].elapsed_time(ph[1]), ph[1].elapsed_time(ph[2])
+    grid_nodes = sum(p.n * p.n for p in plans)
     line = {"metric": "SDE path-steps/s", "value": steps * args.steps / t, "unit": "path-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -384,6 +394,7 @@ def run_batched(args):
                        "interface_nodes": nodes, "path_steps_per_batch": steps,
                        "l2": "flushed between timed steps", "graph": True},
             "meshes_per_s": len(plans) * args.steps / t, "solves_converged": solve_ok,
+            "ms_interface_mc": ms_mc, "ms_fill_and_solves": ms_solve, "grid_nodes": grid_nodes,
             "batch_create_s": t_create, "clocks": clocks,
             "gpu_launches": int(N.sdd_kernel_launches() - launches0)}
     batch.close()
@@ -418,6 +429,69 @@ def run_serve(args):
                                   "std-err <= %g (pilot 1024 paths), dt=5e-5"
                                   % (args.n_max, args.target_stderr),
                       "requests_per_rate": args.count, "results": out}))
+    return 0
+
+
+def run_precision(args):
+    """Precision report for a configuration (default config 4): FP32 stepping
+    on the GPU against the FP64 oracle on an evenly spaced subsample of
+    `sample_nodes` interface nodes, both replaying the same Philox streams of
+    the first `sample_paths` paths (the paired difference is the
+    precision-induced bias, separate from the Monte Carlo error), plus the
+    GPU run at the configuration's full paths per node (std-err per node)."""
+    import torch
+    import oracle
+    from paper_1310_3435_gb300 import native as N
+    torch.cuda.set_device(0)
+    spec = make_spec(args.config)
+    nodes_all = oracle.interface_nodes(spec.n, spec.sx, spec.sy)
+    m = len(nodes_all)
+    idx = (np.arange(args.sample_nodes) * (m // args.sample_nodes)).astype(int)
+    sub = W.MeshSpec(**{**spec.__dict__, "paths": args.sample_paths})
+    out = {"metric": "precision report", "workload": spec.label, "interface_nodes": m,
+           "sample": "%d nodes (every %d-th) x first %d paths" % (len(idx), m // len(idx),
+                                                                  args.sample_paths)}
+    with N.Plan(sub) as P:
+        g32 = N.sdd_interface_mc_sums(P.handle, P.mc_params(precision=W.FP32_STEP))
+    E = oracle.bmap_tables(spec.n, spec.bmap_mode, spec.family, spec.coef_mode, spec.params)
+    t0 = time.perf_counter()
+    o = oracle.mc_nodes(spec.n, nodes_all[idx], E, spec.family, spec.coef_mode, spec.params,
+                        spec.seed, args.sample_paths, spec.dt, spec.cap(), 1e-11, node_ids=idx)
+    t_or = time.perf_counter() - t0
+    x0 = nodes_all[idx] / (spec.n - 1.0)
+    Nn = float(args.sample_paths)
+    m32 = x0 + g32["sum"][idx] / Nn
+    mo = x0 + o["S_all"] / Nn
+    se_o = np.sqrt(np.maximum(o["Q_all"] - o["S_all"] ** 2 / Nn, 0) / (Nn * (Nn - 1)))
+    d = m32 - mo
+    out["fp32_vs_fp64_oracle"] = {
+        "max_abs": float(np.abs(d).max()), "mean_signed": float(d.mean()),
+        "rms": float(np.sqrt((d ** 2).mean())),
+        "max_abs_over_stderr": float((np.abs(d) / se_o).max()),
+        "mc_stderr_median": float(np.median(se_o)), "mc_stderr_max": float(se_o.max()),
+        "steps_rel_diff": float(abs(int(g32["steps"][idx].sum()) - int(o["steps"].sum()))
+                                / o["steps"].sum()),
+        "oracle_ties": int(o["ties"].sum()), "oracle_seconds": t_or}
+    if not args.no_full:
+        full = spec if not args.paths else W.MeshSpec(**{**spec.__dict__, "paths": args.paths})
+        with N.Plan(full) as P:
+            mean = torch.zeros((P.n_nodes, 2), dtype=torch.float64, device="cuda")
+            se = torch.zeros((P.n_nodes, 2), dtype=torch.float64, device="cuda")
+            stream = torch.cuda.Stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            N.sdd_interface_mc(P.handle, P.mc_params(), mean, se, want_stats=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = N.sdd_plan_last_mc_stats(P.handle)
+            sec = e0.elapsed_time(e1) / 1000.0
+            sec_np = se.cpu().numpy()
+        out["full_run"] = {"paths_per_node": full.paths, "path_steps": int(st.path_steps),
+                           "seconds": sec, "path_steps_per_s": st.path_steps / sec,
+                           "stderr_max": float(sec_np.max()),
+                           "stderr_median": float(np.median(sec_np)),
+                           "non_exits": int(st.non_exits)}
+    print(json.dumps(out))
     return 0
 
 
@@ -459,6 +533,11 @@ def main(argv=None):
                     choices=["config1", "config2", "config3", "config4"])
     ap.add_argument("--count", type=int, default=256, help="meshes (config3) or requests (--serve)")
     ap.add_argument("--serve", action="store_true", help="serving run (config 5) instead")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="FP32 stepping vs the FP64 oracle on a node subsample (+ full-N run)")
+    ap.add_argument("--sample-nodes", type=int, default=64)
+    ap.add_argument("--sample-paths", type=int, default=4096)
+    ap.add_argument("--no-full", action="store_true")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
     ap.add_argument("--n-max", type=int, default=1025)
     ap.add_argument("--target-stderr", type=float, default=1e-3)
@@ -479,6 +558,8 @@ def main(argv=None):
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.precision_report:
+        return run_precision(args)
     if args.config == "config3":
         return run_batched(args)
     return run_native(args)

@@ -238,6 +238,11 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
  * (needs a non-default stream). */
 int sdd_batch_run(sdd_batch* batch, int use_graph, void* stream);
 
+/* Enqueues one phase of a run, without a graph: phases = 1 Monte Carlo only,
+ * 2 fill + subdomain solves only (from the interface values already in the
+ * plans), 3 both.  For timing the phases separately. */
+int sdd_batch_run_phases(sdd_batch* batch, int phases, void* stream);
+
 /* Statistics of plan `index` in the batch's last run (synchronises). */
 int sdd_batch_plan_stats(sdd_batch* batch, int index, sdd_mc_stats* mc, sdd_solve_stats* solve);
 

@@ -39,6 +39,7 @@ int cuda_status(cudaError_t e, const char* what)
     return SDD_ERR_CUDA;
 }
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+uint64_t launches_now() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -465,6 +466,7 @@ struct sdd_batch {
     int n_subs = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_kernels = 0;                 // kernels in one replay of the graph
     cudaStream_t last_stream = nullptr;
     bool ran = false;
 };
@@ -492,27 +494,32 @@ void batch_free(sdd_batch* b)
 
 // Enqueues one whole run of the batch on `stream` (no host synchronisation,
 // no device queries: safe inside a stream capture).
-int batch_enqueue(sdd_batch* b, cudaStream_t stream)
+int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
 {
     const size_t np = b->plans.size();
-    for (sdd_plan* p : b->plans) {                 // first run: edge coefficients
-        int rc = ensure_coefs(p, stream);
-        if (rc) return rc;
+    if (phases & 1) {
+        SDD_CUDA(cudaMemsetAsync(b->d_stats, 0, np * sizeof(McStatsDev), stream));
+        for (const McGroup& g : b->groups) {
+            int rc = launch_mc_sized(g.args, g.precision, g.fc, g.blocks, stream);
+            if (rc) return rc;
+        }
     }
-    SDD_CUDA(cudaMemsetAsync(b->d_stats, 0, np * sizeof(McStatsDev), stream));
-    for (const McGroup& g : b->groups) {
-        int rc = launch_mc_sized(g.args, g.precision, g.fc, g.blocks, stream);
+    if (phases & 2) {
+        for (sdd_plan* p : b->plans) {                 // first solve: edge coefficients
+            int rc = ensure_coefs(p, stream);
+            if (rc) return rc;
+        }
+        int rc = launch_fill_batched(b->d_fill, b->d_fill_off, (int)np, b->fill_total, stream);
         if (rc) return rc;
+        SolveArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.meshes = b->d_smesh;
+        sa.subs = b->d_subs;
+        sa.n_subs = b->n_subs;
+        sa.stats = b->d_substats;
+        return launch_solve(sa, stream);
     }
-    int rc = launch_fill_batched(b->d_fill, b->d_fill_off, (int)np, b->fill_total, stream);
-    if (rc) return rc;
-    SolveArgs sa;
-    memset(&sa, 0, sizeof(sa));
-    sa.meshes = b->d_smesh;
-    sa.subs = b->d_subs;
-    sa.n_subs = b->n_subs;
-    sa.stats = b->d_substats;
-    return launch_solve(sa, stream);
+    return SDD_OK;
 }
 
 }  // namespace
@@ -1017,7 +1024,10 @@ int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
             return fail(SDD_ERR_INVALID_ARG, "a graph launch needs a non-default stream");
         if (!b->graph_exec) {
             SDD_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            const uint64_t c0 = launches_now();
             rc = batch_enqueue(b, stream);
+            b->graph_kernels = launches_now() - c0;
+            count_launch(0 - b->graph_kernels);          // captured, not launched yet
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(stream, &g);
             if (rc) {
@@ -1029,6 +1039,7 @@ int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
             SDD_CUDA(cudaGraphInstantiate(&b->graph_exec, b->graph, 0));
         }
         SDD_CUDA(cudaGraphLaunch(b->graph_exec, stream));
+        count_launch(b->graph_kernels);
     } else {
         if ((rc = batch_enqueue(b, stream))) return rc;
     }
@@ -1042,6 +1053,34 @@ int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
             p->mc_done = nullptr;
         }
     }
+    b->last_stream = stream;
+    b->ran = true;
+    return SDD_OK;
+}
+
+int sdd_batch_run_phases(sdd_batch* b, int phases, void* stream_)
+{
+    clear_error();
+    if (!b) return fail(SDD_ERR_INVALID_ARG, "batch is NULL");
+    if (phases < 1 || phases > 3) return fail(SDD_ERR_INVALID_ARG, "phases must be 1, 2 or 3");
+    int dev = -1;
+    SDD_CUDA(cudaGetDevice(&dev));
+    if (dev != b->device) return fail(SDD_ERR_INVALID_ARG, "batch belongs to another device");
+    cudaStream_t stream = as_stream(stream_);
+    int rc = batch_enqueue(b, stream, phases);
+    if (rc) return rc;
+    if (phases & 1) {
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            sdd_plan* p = b->plans[i];
+            p->last_paths = b->plan_paths[i];
+            p->have_mc = true;
+            if (p->mc_done) {
+                cudaEventDestroy(p->mc_done);
+                p->mc_done = nullptr;
+            }
+        }
+    }
+    for (sdd_plan* p : b->plans) p->last_stream = stream;
     b->last_stream = stream;
     b->ran = true;
     return SDD_OK;

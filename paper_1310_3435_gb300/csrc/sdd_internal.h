@@ -17,7 +17,8 @@ void clear_error();
 int fail(int code, const std::string& msg);
 // Records a CUDA error (if any) and returns SDD_ERR_CUDA, else SDD_OK.
 int cuda_status(cudaError_t e, const char* what);
-void count_launch(uint64_t k = 1);
+void count_launch(uint64_t k = 1);       // kernels launched (wraps modulo 2^64)
+uint64_t launches_now();
 
 #define SDD_CUDA(call)                                                  \
     do {                                                                \

@@ -141,13 +141,14 @@ def load(build_if_missing: bool = True):
     L.sdd_batch_create.argtypes = [P(vp), ctypes.c_int, P(sdd_mc_params), P(sdd_solve_params),
                                    P(vp)]
     L.sdd_batch_run.argtypes = [vp, ctypes.c_int, vp]
+    L.sdd_batch_run_phases.argtypes = [vp, ctypes.c_int, vp]
     L.sdd_batch_plan_stats.argtypes = [vp, ctypes.c_int, P(sdd_mc_stats), P(sdd_solve_stats)]
     L.sdd_batch_destroy.argtypes = [vp]
     L.sdd_batch_destroy.restype = None
     for name in ("sdd_mesh_plan", "sdd_plan_num_nodes", "sdd_plan_nodes", "sdd_plan_edges",
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
                  "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
-                 "sdd_plan_results", "sdd_batch_create", "sdd_batch_run",
+                 "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
                  "sdd_batch_plan_stats"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -328,6 +329,10 @@ def sdd_batch_run(batch, use_graph: bool = False, stream=None) -> None:
     _check(load().sdd_batch_run(batch, 1 if use_graph else 0, _stream(stream)), "sdd_batch_run")
 
 
+def sdd_batch_run_phases(batch, phases: int, stream=None) -> None:
+    _check(load().sdd_batch_run_phases(batch, int(phases), _stream(stream)), "sdd_batch_run_phases")
+
+
 def sdd_batch_plan_stats(batch, index: int, allow_not_converged: bool = False):
     ms, ss = sdd_mc_stats(), sdd_solve_stats()
     allow = (SDD_ERR_NOT_CONVERGED,) if allow_not_converged else ()
@@ -419,6 +424,9 @@ class Batch:
 
     def run(self, use_graph: bool = False, stream=None) -> None:
         sdd_batch_run(self.handle, use_graph, stream)
+
+    def run_phases(self, phases: int, stream=None) -> None:
+        sdd_batch_run_phases(self.handle, phases, stream)
 
     def stats(self, index: int, allow_not_converged: bool = False):
         return sdd_batch_plan_stats(self.handle, index, allow_not_converged)

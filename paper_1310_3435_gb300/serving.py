@@ -99,7 +99,7 @@ class Server:
     def __init__(self, hbm_budget: float = 150e9, n_streams: int = 3, max_batch: int = 256,
                  target_stderr: float | None = 1e-3, pilot_paths: int = 1024,
                  min_paths: int = 1024, max_paths: int = 4_000_000, use_graph: bool = False,
-                 backend=None, cuda=None, sms: int | None = None):
+                 max_wait: float = 0.25, backend=None, cuda=None, sms: int | None = None):
         """backend / cuda: the library binding and the stream/event provider
         (default: paper_1310_3435_gb300.native and torch.cuda); tests of the
         host logic pass stand-ins."""
@@ -116,6 +116,7 @@ class Server:
         self.min_paths = min_paths
         self.max_paths = max_paths
         self.use_graph = use_graph
+        self.max_wait = max_wait
         self.streams = [cuda.Stream() for _ in range(n_streams)]
         self.pilot_stream = cuda.Stream()
         self.sms = sms or cuda.get_device_properties(cuda.current_device()).multi_processor_count
@@ -178,8 +179,13 @@ class Server:
                 self.peak_used = max(self.peak_used, self.used)
                 ready.append([req, plan, paths, nbytes, ta])
                 progressed = True
-            # 3. launch everything ready as one batch on a free stream
-            if ready and free_streams:
+            # 3. launch the ready requests as one batch on a free stream: at once
+            # when the device is idle; while a batch runs, let the ready queue
+            # fill up (to max_batch, or until its oldest request has waited
+            # max_wait seconds) so that the next batch is a large one
+            fill = (not inflight or len(ready) >= self.max_batch
+                    or (ready and now() - ready[0][4] >= self.max_wait))
+            if ready and free_streams and fill:
                 take = [ready.popleft() for _ in range(min(self.max_batch, len(ready)))]
                 plans = [x[1] for x in take]
                 mcs = [p.mc_params(paths=x[2]) for p, x in zip(plans, take)]
