@@ -99,6 +99,16 @@ void dev_free(T*& p, cudaStream_t s)
     p = nullptr;
 }
 
+// Subdomains in decreasing interior size: one CTA each, the largest (the
+// longest solves) are scheduled first, so they do not set the tail.
+void sort_largest_first(std::vector<SubDev>& v)
+{
+    auto size = [](const SubDev& d) {
+        return (int64_t)std::max(d.i1 - d.i0 - 1, 0) * std::max(d.j1 - d.j0 - 1, 0);
+    };
+    std::stable_sort(v.begin(), v.end(), [&](const SubDev& a, const SubDev& b) { return size(a) > size(b); });
+}
+
 // Interface lines of an s-way split of n points: I_k = round(k (n-1)/s),
 // halves rounded up, exact integer arithmetic.
 std::vector<int> interface_lines(int n, int s)
@@ -401,6 +411,7 @@ int run_solve(sdd_plan* p, const double* iface_dev, const sdd_solve_params* sp,
     a.single = sm;
     a.subs = p->d_subs;
     a.n_subs = (int)p->h_subs.size();
+    a.solver_mask = sp->solver == SDD_SOLVER_SOR ? 1 : 2;
     a.stats = p->d_substats;
     if ((rc = launch_solve(a, stream))) return rc;
     p->last_stream = stream;
@@ -464,6 +475,7 @@ struct sdd_batch {
     sdd::SubStat* d_substats = nullptr;
     std::vector<int> sub_begin;                 // plan -> first subdomain
     int n_subs = 0;
+    int solver_mask = 0;                        // solvers used by the batch's plans
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t graph_kernels = 0;                 // kernels in one replay of the graph
@@ -516,6 +528,7 @@ int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
         sa.meshes = b->d_smesh;
         sa.subs = b->d_subs;
         sa.n_subs = b->n_subs;
+        sa.solver_mask = b->solver_mask;
         sa.stats = b->d_substats;
         return launch_solve(sa, stream);
     }
@@ -584,7 +597,11 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
     Y.insert(Y.end(), p->iy.begin(), p->iy.end());
     Y.push_back(n - 1);
     for (int b = 0; b < sy; ++b)
-        for (int a = 0; a < sx; ++a) p->h_subs.push_back(SubDev{0, X[a], X[a + 1], Y[b], Y[b + 1]});
+        for (int a = 0; a < sx; ++a) {
+            const int32_t slot = (int32_t)p->h_subs.size();
+            p->h_subs.push_back(SubDev{0, X[a], X[a + 1], Y[b], Y[b + 1], slot});
+        }
+    sort_largest_first(p->h_subs);
 
     // boundary tables [2][4][n]
     p->h_edges.assign((size_t)8 * n, 0.0);
@@ -925,6 +942,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         memset(&r, 0, sizeof(r));
         r.n = p->n;
         r.solver = sp[i].solver;
+        b->solver_mask |= sp[i].solver == SDD_SOLVER_SOR ? 1 : 2;
         r.max_iter = sp[i].max_iter > 0 ? sp[i].max_iter : (sp[i].solver == SDD_SOLVER_SOR ? 200000 : 20000);
         r.tol = sp[i].tol;
         r.omega = sp[i].omega;
@@ -946,11 +964,13 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         b->sub_begin.push_back((int)subs.size());
         for (SubDev d : p->h_subs) {
             d.mesh = i;
+            d.slot += b->sub_begin.back();      // stats in plan order, plan by plan
             subs.push_back(d);
         }
     }
     b->n_subs = (int)subs.size();
     b->fill_total = fill_off[n_plans];
+    sort_largest_first(subs);
 
     const size_t ng = gi.size();
     if ((rc = dev_alloc(&b->d_meshes, recs.size())) || (rc = dev_alloc(&b->d_offs, offs.size())) ||

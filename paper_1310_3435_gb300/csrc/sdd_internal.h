@@ -130,6 +130,7 @@ struct SolveMeshDev {
 struct SubDev {
     int32_t mesh;           // index into the SolveMeshDev array
     int32_t i0, i1, j0, j1; // interior: i0 < i < i1, j0 < j < j1
+    int32_t slot;           // index of its SubStat record
 };
 
 struct SubStat {
@@ -153,6 +154,7 @@ struct SolveArgs {
     SolveMeshDev single;
     const SubDev* subs;
     int n_subs;
+    int solver_mask;            // bit 0: some subdomain uses SOR, bit 1: CG
     SubStat* stats;
 };
 int launch_solve(const SolveArgs& args, cudaStream_t stream);

@@ -4,7 +4,8 @@
 //     sum_nbr c_edge (u_nbr - u_ij) = 0,   c at edge midpoints  (§3.2)
 // is solved independently, once (no iteration between subdomains).
 //
-// One CTA per subdomain, all subdomains of all meshes in one launch.  The mesh
+// One CTA (1024 threads) per subdomain, all subdomains of all meshes in one
+// launch, largest subdomains first (they set the end of the launch).  The mesh
 // u is FP64 [n][n][2] (the two components share the operator and are solved
 // together, interleaved as double2).  Two solvers:
 //   * red-black SOR in FP64;
@@ -21,7 +22,13 @@
 namespace sdd {
 namespace {
 
-constexpr int SOLVE_THREADS = 512;
+#ifndef SDD_SOLVE_THREADS
+#define SDD_SOLVE_THREADS 1024
+#endif
+#ifndef SDD_SOLVE_MIN_BLOCKS
+#define SDD_SOLVE_MIN_BLOCKS 1
+#endif
+constexpr int SOLVE_THREADS = SDD_SOLVE_THREADS;
 
 // ------------------------------------------------------ coefficients ----
 // c(s,t) = w or 1/w for the three density families, FP64.
@@ -225,20 +232,29 @@ __device__ double rhs_norm2(const SolveMeshDev& M, const Box& B, double* scratch
     double acc[1] = {0.0};
     for (int t = threadIdx.x; t < B.nx * B.ny; t += blockDim.x) {
         const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
-        if (i != B.i0 + 1 && i != B.i1 - 1 && j != B.j0 + 1 && j != B.j1 - 1) continue;
+        const bool w = i == B.i0 + 1, e = i == B.i1 - 1, s = j == B.j0 + 1, nn = j == B.j1 - 1;
+        if (!(w | e | s | nn)) continue;
         const int64_t id = (int64_t)j * n + i;
         double bx = 0.0, by = 0.0;
-        const int ni[4] = {i + 1, i - 1, i, i};
-        const int nj[4] = {j, j, j + 1, j - 1};
-        const double cc[4] = {M.cx[(int64_t)j * (n - 1) + i], M.cx[(int64_t)j * (n - 1) + i - 1],
-                              M.cy[id], M.cy[id - n]};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!B.interior(ni[q], nj[q])) {
-                const double2 v = u[(int64_t)nj[q] * n + ni[q]];
-                bx += cc[q] * v.x;
-                by += cc[q] * v.y;
-            }
+        if (e) {
+            const double c = M.cx[(int64_t)j * (n - 1) + i];
+            const double2 v = u[id + 1];
+            bx += c * v.x; by += c * v.y;
+        }
+        if (w) {
+            const double c = M.cx[(int64_t)j * (n - 1) + i - 1];
+            const double2 v = u[id - 1];
+            bx += c * v.x; by += c * v.y;
+        }
+        if (nn) {
+            const double c = M.cy[id];
+            const double2 v = u[id + n];
+            bx += c * v.x; by += c * v.y;
+        }
+        if (s) {
+            const double c = M.cy[id - n];
+            const double2 v = u[id - n];
+            bx += c * v.x; by += c * v.y;
         }
         acc[0] += bx * bx + by * by;
     }
@@ -453,7 +469,10 @@ __device__ void cg_box(const SolveMeshDev& M, const Box& B, SubStat& st, double*
     st.converged = r2 <= goal ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(SOLVE_THREADS)
+// MASK: solvers compiled into the kernel (bit 0 SOR, bit 1 CG), so a launch
+// whose subdomains all use one solver gets a kernel with that solver only.
+template <int MASK>
+__global__ void __launch_bounds__(SOLVE_THREADS, SDD_SOLVE_MIN_BLOCKS)
 k_solve(SolveArgs a)
 {
     __shared__ double scratch[128];
@@ -465,10 +484,14 @@ k_solve(SolveArgs a)
     st.converged = 1;
     st.rel_residual = 0.0;
     if (B.nx > 0 && B.ny > 0) {
-        if (M.solver == SDD_SOLVER_CG_FP32_REFINE) cg_box(M, B, st, scratch);
-        else sor_box(M, B, st, scratch);
+        if constexpr (MASK == 2) cg_box(M, B, st, scratch);
+        else if constexpr (MASK == 1) sor_box(M, B, st, scratch);
+        else {
+            if (M.solver == SDD_SOLVER_CG_FP32_REFINE) cg_box(M, B, st, scratch);
+            else sor_box(M, B, st, scratch);
+        }
     }
-    if (threadIdx.x == 0) a.stats[blockIdx.x] = st;
+    if (threadIdx.x == 0) a.stats[sd.slot] = st;
 }
 
 }  // namespace
@@ -519,7 +542,9 @@ int launch_solve(const SolveArgs& args, cudaStream_t stream)
     k_coons<<<args.n_subs, 256, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
-    k_solve<<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
+    if (args.solver_mask == 1) k_solve<1><<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
+    else if (args.solver_mask == 2) k_solve<2><<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
+    else k_solve<3><<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
     return SDD_OK;
