@@ -345,8 +345,24 @@ def run_batched(args):
         specs = [W.MeshSpec(**{**sp.__dict__, "paths": args.paths}) for sp in specs]
     plans = [N.Plan(sp) for sp in specs]
     stream = torch.cuda.Stream()
+    tuned = None
+    t_tune = 0.0
+    mcs = [p.mc_params() for p in plans]
+    sps = [p.solve_params() for p in plans]
+    if not args.no_autotune:
+        from paper_1310_3435_gb300 import autotune
+        t0 = time.perf_counter()
+        tuner = autotune.Autotuner()
+        picks = [tuner.tune(sp, p.n_nodes) for sp, p in zip(specs, plans)]
+        tuner.save()
+        t_tune = time.perf_counter() - t0
+        mcs = [p.mc_params(chunk=k["chunk"]) for p, k in zip(plans, picks)]
+        sps = [p.solve_params(block_threads=k["block_threads"]) for p, k in zip(plans, picks)]
+        tuned = {"buckets_timed": tuner.timed, "seconds": t_tune,
+                 "block_threads": sorted({k["block_threads"] for k in picks}),
+                 "chunks": sorted({k["chunk"] for k in picks})}
     t0 = time.perf_counter()
-    batch = N.Batch(plans)
+    batch = N.Batch(plans, mcs, sps)
     t_create = time.perf_counter() - t0
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -395,7 +411,7 @@ def run_batched(args):
                        "l2": "flushed between timed steps", "graph": True},
             "meshes_per_s": len(plans) * args.steps / t, "solves_converged": solve_ok,
             "ms_interface_mc": ms_mc, "ms_fill_and_solves": ms_solve, "grid_nodes": grid_nodes,
-            "batch_create_s": t_create, "clocks": clocks,
+            "batch_create_s": t_create, "autotune": tuned, "clocks": clocks,
             "gpu_launches": int(N.sdd_kernel_launches() - launches0)}
     batch.close()
     for p in plans:
@@ -538,6 +554,7 @@ def main(argv=None):
     ap.add_argument("--sample-nodes", type=int, default=64)
     ap.add_argument("--sample-paths", type=int, default=4096)
     ap.add_argument("--no-full", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
     ap.add_argument("--n-max", type=int, default=1025)
     ap.add_argument("--target-stderr", type=float, default=1e-3)

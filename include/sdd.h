@@ -146,6 +146,9 @@ typedef struct {
     int32_t max_iter;                  /* sweeps (SOR) or inner iterations (CG); 0 = default */
     double tol;                        /* relative residual ||b - A u||_2 / ||b||_2 per subdomain */
     double omega;                      /* SOR relaxation; 0 = per-subdomain estimate */
+    int32_t block_threads;             /* threads per subdomain CTA: 256, 512, 1024; 0 = 1024
+                                          (in a batch: the largest requested) */
+    int32_t reserved;
 } sdd_solve_params;
 
 typedef struct {

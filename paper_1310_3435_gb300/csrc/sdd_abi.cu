@@ -379,6 +379,9 @@ int validate_solve(const sdd_solve_params* sp)
     if (sp->max_iter < 0) return fail(SDD_ERR_INVALID_ARG, "max_iter must be >= 0");
     if (!(sp->omega == 0.0 || (sp->omega > 0.0 && sp->omega < 2.0)))
         return fail(SDD_ERR_INVALID_ARG, "omega must be 0 or in (0, 2)");
+    if (sp->block_threads != 0 && sp->block_threads != 256 && sp->block_threads != 512 &&
+        sp->block_threads != 1024)
+        return fail(SDD_ERR_INVALID_ARG, "block_threads must be 0, 256, 512 or 1024");
     return SDD_OK;
 }
 
@@ -412,6 +415,7 @@ int run_solve(sdd_plan* p, const double* iface_dev, const sdd_solve_params* sp,
     a.subs = p->d_subs;
     a.n_subs = (int)p->h_subs.size();
     a.solver_mask = sp->solver == SDD_SOLVER_SOR ? 1 : 2;
+    a.threads = sp->block_threads;
     a.stats = p->d_substats;
     if ((rc = launch_solve(a, stream))) return rc;
     p->last_stream = stream;
@@ -476,6 +480,7 @@ struct sdd_batch {
     std::vector<int> sub_begin;                 // plan -> first subdomain
     int n_subs = 0;
     int solver_mask = 0;                        // solvers used by the batch's plans
+    int solve_threads = 0;                      // largest CTA size requested (0: default)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t graph_kernels = 0;                 // kernels in one replay of the graph
@@ -529,6 +534,7 @@ int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
         sa.subs = b->d_subs;
         sa.n_subs = b->n_subs;
         sa.solver_mask = b->solver_mask;
+        sa.threads = b->solve_threads;
         sa.stats = b->d_substats;
         return launch_solve(sa, stream);
     }
@@ -943,6 +949,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         r.n = p->n;
         r.solver = sp[i].solver;
         b->solver_mask |= sp[i].solver == SDD_SOLVER_SOR ? 1 : 2;
+        b->solve_threads = std::max(b->solve_threads, (int)sp[i].block_threads);
         r.max_iter = sp[i].max_iter > 0 ? sp[i].max_iter : (sp[i].solver == SDD_SOLVER_SOR ? 200000 : 20000);
         r.tol = sp[i].tol;
         r.omega = sp[i].omega;

@@ -155,6 +155,7 @@ struct SolveArgs {
     const SubDev* subs;
     int n_subs;
     int solver_mask;            // bit 0: some subdomain uses SOR, bit 1: CG
+    int threads;                // CTA size: 256, 512 or 1024 (other: 1024)
     SubStat* stats;
 };
 int launch_solve(const SolveArgs& args, cudaStream_t stream);

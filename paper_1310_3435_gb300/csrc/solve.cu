@@ -22,13 +22,9 @@
 namespace sdd {
 namespace {
 
-#ifndef SDD_SOLVE_THREADS
-#define SDD_SOLVE_THREADS 1024
-#endif
-#ifndef SDD_SOLVE_MIN_BLOCKS
-#define SDD_SOLVE_MIN_BLOCKS 1
-#endif
-constexpr int SOLVE_THREADS = SDD_SOLVE_THREADS;
+// CTA sizes a solve can be launched with (SolveArgs::threads); 1024 is the
+// default, smaller CTAs suit small subdomains (more CTAs per SM).
+constexpr int SOLVE_THREADS_DEFAULT = 1024;
 
 // ------------------------------------------------------ coefficients ----
 // c(s,t) = w or 1/w for the three density families, FP64.
@@ -471,8 +467,8 @@ __device__ void cg_box(const SolveMeshDev& M, const Box& B, SubStat& st, double*
 
 // MASK: solvers compiled into the kernel (bit 0 SOR, bit 1 CG), so a launch
 // whose subdomains all use one solver gets a kernel with that solver only.
-template <int MASK>
-__global__ void __launch_bounds__(SOLVE_THREADS, SDD_SOLVE_MIN_BLOCKS)
+template <int MASK, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
 k_solve(SolveArgs a)
 {
     __shared__ double scratch[128];
@@ -542,9 +538,12 @@ int launch_solve(const SolveArgs& args, cudaStream_t stream)
     k_coons<<<args.n_subs, 256, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
-    if (args.solver_mask == 1) k_solve<1><<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
-    else if (args.solver_mask == 2) k_solve<2><<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
-    else k_solve<3><<<args.n_subs, SOLVE_THREADS, 0, stream>>>(args);
+    const int t = args.threads == 256 || args.threads == 512 ? args.threads : SOLVE_THREADS_DEFAULT;
+    void (*k)(SolveArgs) = nullptr;
+    if (t == 256) k = args.solver_mask == 1 ? k_solve<1, 256> : args.solver_mask == 2 ? k_solve<2, 256> : k_solve<3, 256>;
+    else if (t == 512) k = args.solver_mask == 1 ? k_solve<1, 512> : args.solver_mask == 2 ? k_solve<2, 512> : k_solve<3, 512>;
+    else k = args.solver_mask == 1 ? k_solve<1, 1024> : args.solver_mask == 2 ? k_solve<2, 1024> : k_solve<3, 1024>;
+    k<<<args.n_subs, t, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
     return SDD_OK;

@@ -81,7 +81,8 @@ assert NODE_SUMS_DTYPE.itemsize == ctypes.sizeof(sdd_node_sums)
 
 class sdd_solve_params(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("tol", ctypes.c_double), ("omega", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("omega", ctypes.c_double),
+                ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sdd_solve_stats(ctypes.Structure):
@@ -250,12 +251,13 @@ def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, c
 
 
 def solve_params(solver: int = SDD_SOLVER_SOR, tol: float = 1e-10, max_iter: int = 0,
-                 omega: float = 0.0) -> sdd_solve_params:
+                 omega: float = 0.0, block_threads: int = 0) -> sdd_solve_params:
     s = sdd_solve_params()
     s.solver = int(solver)
     s.tol = float(tol)
     s.max_iter = int(max_iter)
     s.omega = float(omega)
+    s.block_threads = int(block_threads)
     return s
 
 

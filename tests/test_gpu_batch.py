@@ -90,3 +90,24 @@ def test_batch_launch_count_and_validation():
             B.run(use_graph=True, stream=None)     # graphs need a non-default stream
     for P in plans:
         P.close()
+
+
+def test_autotuned_parameters_are_valid_and_keep_results(tmp_path):
+    import torch
+    from paper_1310_3435_gb300 import autotune
+    from paper_1310_3435_gb300 import native as N
+    spec = W.config3(count=1, seed=4, paths=512, dt=2e-4)[0]
+    tuner = autotune.Autotuner(path=str(tmp_path / "t.json"), probe_paths=256)
+    pick = tuner.tune(spec)
+    assert pick["chunk"] in autotune.CHUNKS and pick["block_threads"] in autotune.SOLVE_THREADS
+    assert tuner.timed == 6
+    assert tuner.tune(spec) == pick and tuner.timed == 6          # cached
+    base = _alone(spec)
+    with gpu_plan(spec) as P:
+        mesh = np.zeros((spec.n, spec.n, 2))
+        mean = np.zeros((P.n_nodes, 2))
+        se = np.zeros((P.n_nodes, 2))
+        N.sdd_mesh_generate(P.handle, P.mc_params(chunk=pick["chunk"]),
+                            P.solve_params(block_threads=pick["block_threads"]), mesh, mean, se)
+    assert np.allclose(mean, base[1], rtol=0, atol=1e-14)
+    assert np.allclose(mesh, base[0], rtol=0, atol=1e-12)
