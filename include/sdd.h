@@ -89,6 +89,16 @@ extern "C" {
 #define SDD_FP64      0
 #define SDD_FP32_STEP 1
 
+/* exit test of a step (§2.2): at the end of the step only, or also the
+ * Brownian-bridge test: a step x -> y that stayed inside crossed side s with
+ * probability exp(-d_s(x) d_s(y) / dt) (d_s = distance to side s, noise
+ * sqrt(2) dW), decided by the uniforms of Philox counter (k, path, node, 1) in
+ * the side order s=0, s=1, t=0, t=1; skipped when every product is >= 23 dt
+ * (probability below 2^-33); exit point: the side, with the mean of the two
+ * tangential coordinates.  Cuts the O(sqrt(dt)) exit bias to O(dt). */
+#define SDD_EXIT_END_OF_STEP 0
+#define SDD_EXIT_BRIDGE      1
+
 /* subdomain solvers */
 #define SDD_SOLVER_SOR            0   /* FP64 red-black SOR */
 #define SDD_SOLVER_CG_FP32_REFINE 1   /* FP32 Jacobi-PCG inner solves + FP64 iterative refinement */
@@ -118,6 +128,8 @@ typedef struct {
                                           multiple of 32, at most 8192 */
     uint64_t max_steps;                /* step cap per path, 0 = ceil(2/dt) */
     double tie_delta;                  /* <0: default (1e-11 FP64, 0 FP32) */
+    int32_t exit_test;                 /* SDD_EXIT_END_OF_STEP | SDD_EXIT_BRIDGE */
+    int32_t reserved;
 } sdd_mc_params;
 
 typedef struct {

@@ -74,14 +74,19 @@ def lib():
         L.oracle_path.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_uint32, ctypes.c_uint32, dp, ctypes.c_int,
                                   ctypes.c_int, dp, ctypes.c_uint64, ctypes.c_double,
-                                  ctypes.c_uint64, ctypes.c_double, dp, u64p, ip, ip]
+                                  ctypes.c_uint64, ctypes.c_double, ctypes.c_int, dp, u64p, ip,
+                                  ip]
         L.oracle_path.restype = None
         L.oracle_mc_node.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_uint32, dp, ctypes.c_int, ctypes.c_int, dp,
                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_double,
-                                     dp, u64p]
+                                     ctypes.c_int, dp, u64p]
         L.oracle_mc_node.restype = None
+        L.oracle_bridge_exit.argtypes = [ctypes.c_double] * 5 + [ctypes.c_uint64, ctypes.c_uint32,
+                                                                 ctypes.c_uint32, ctypes.c_uint32,
+                                                                 dp, ip]
+        L.oracle_bridge_exit.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -220,11 +225,13 @@ def default_threads() -> int:
 
 def mc_nodes(n: int, nodes, edges: np.ndarray, family: int, coef_mode: int, params,
              seed: int, paths: int, dt: float, max_steps: int, tie_delta: float = 0.0,
-             node_ids=None, threads: int | None = None, path_begin: int = 0) -> dict:
+             node_ids=None, threads: int | None = None, path_begin: int = 0,
+             exit_test: int = 0) -> dict:
     """Per-node Monte Carlo sums (§2.2) for nodes [(i, j), ...].
 
     Node m uses counter word node_ids[m] (default: m) and paths
-    [path_begin, path_begin + paths).  Returns arrays
+    [path_begin, path_begin + paths).  exit_test: 0 end-of-step test only,
+    1 also the Brownian-bridge test (§2.2).  Returns arrays
       S_all, Q_all, S_nt, Q_nt : [n_nodes, 2]  sums of d = F - X0 and d^2 over
                                  all paths / paths not flagged as ties
       paths, ties, non_exits, steps : [n_nodes] uint64
@@ -244,7 +251,8 @@ def mc_nodes(n: int, nodes, edges: np.ndarray, family: int, coef_mode: int, para
         crow = counts[k]
         L.oracle_mc_node(n, i, j, int(ids[k]) & 0xFFFFFFFF, _dp(E), family, coef_mode,
                          _dp(p), seed, path_begin, path_begin + paths, dt, max_steps,
-                         tie_delta, srow.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         tie_delta, exit_test,
+                         srow.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          crow.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
 
     nt = threads or default_threads()
@@ -275,7 +283,7 @@ def mc_estimate(nodes, n: int, S: np.ndarray, Q: np.ndarray, N) -> tuple:
 
 def path(n: int, s0: float, t0: float, node: int, path_index: int, edges: np.ndarray,
          family: int, coef_mode: int, params, seed: int, dt: float, max_steps: int,
-         tie_delta: float = 0.0) -> dict:
+         tie_delta: float = 0.0, exit_test: int = 0) -> dict:
     """One path from (s0, t0): score, step count, tie and cap flags."""
     E = np.ascontiguousarray(edges, dtype=np.float64)
     p = _params(params)
@@ -284,7 +292,7 @@ def path(n: int, s0: float, t0: float, node: int, path_index: int, edges: np.nda
     tie = ctypes.c_int()
     cap = ctypes.c_int()
     lib().oracle_path(n, s0, t0, node, path_index, _dp(E), family, coef_mode, _dp(p),
-                      seed, dt, max_steps, tie_delta, _dp(F), ctypes.byref(st),
+                      seed, dt, max_steps, tie_delta, exit_test, _dp(F), ctypes.byref(st),
                       ctypes.byref(tie), ctypes.byref(cap))
     return {"F": F, "steps": int(st.value), "tie": bool(tie.value), "capped": bool(cap.value)}
 
@@ -294,6 +302,15 @@ def exit_point(xs: float, xt: float, ys: float, yt: float):
     e = np.zeros(2, dtype=np.float64)
     edge = lib().oracle_exit_point(xs, xt, ys, yt, _dp(e))
     return edge, e
+
+
+def bridge_exit(xs, xt, ys, yt, dt, seed, node, path_index, k):
+    """(edge or -1, exit point, tie) of the Brownian-bridge test of step k."""
+    e = np.zeros(2, dtype=np.float64)
+    tie = ctypes.c_int(0)
+    edge = lib().oracle_bridge_exit(xs, xt, ys, yt, dt, seed, node, path_index, k, _dp(e),
+                                    ctypes.byref(tie))
+    return edge, e, bool(tie.value)
 
 
 def lookup(table, tau: float) -> float:

@@ -233,6 +233,53 @@ static int nearest_side(double s, double t, double e[2])
     return edge_of[best];
 }
 
+/* ------------------------------------------------------- Brownian bridge -- */
+/* Brownian-bridge exit test (§2.2, after Gobet): given the end points x, y of
+ * an Euler-Maruyama step that stayed inside, the process sqrt(2) W pinned at x
+ * and y crossed the side s during the step with probability
+ *   p_s = exp(-2 d_s(x) d_s(y) / (sigma^2 dt)) = exp(-d_s(x) d_s(y) / dt),
+ * d_s = distance to side s (half-space approximation of the square).  Sides in
+ * the order s=0, s=1, t=0, t=1 draw the uniforms U_m = (r_m + 1/2) 2^-32 of
+ * Philox(counter = (k, path, node, 1)), k = index of the step; the first side
+ * with U_m < p_m is crossed.  When d_s(x) d_s(y) >= 23 dt for every side no
+ * crossing is possible (p < 2^-33 <= U), so no uniforms are drawn.  The exit
+ * point is the side value with the mean of the two tangential coordinates.
+ * Returns the edge crossed or -1; *tie = 1 if some |U - p| < 1e-12. */
+int oracle_bridge_exit(double xs, double xt, double ys, double yt, double dt, uint64_t seed,
+                       uint32_t node, uint32_t path, uint32_t k, double e[2], int* tie)
+{
+    double q[4] = {xs * ys, (1.0 - xs) * (1.0 - ys), xt * yt, (1.0 - xt) * (1.0 - yt)};
+    int any = 0;
+    for (int m = 0; m < 4; ++m)
+        if (q[m] < 23.0 * dt) any = 1;
+    if (!any) return -1;
+    uint32_t ctr[4] = {k, path, node, 1u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    static const int edge_of[4] = {2, 3, 0, 1};
+    for (int m = 0; m < 4; ++m) {
+        if (!(q[m] < 23.0 * dt)) continue;
+        double p = exp(-q[m] / dt);
+        double u = ((double)r[m] + 0.5) * 0x1p-32;
+        if (fabs(u - p) < 1e-12) *tie = 1;
+        if (u < p) {
+            double ts = 0.5 * (xs + ys), tt = 0.5 * (xt + yt);
+            if (ts < 0.0) ts = 0.0;
+            if (ts > 1.0) ts = 1.0;
+            if (tt < 0.0) tt = 0.0;
+            if (tt > 1.0) tt = 1.0;
+            e[0] = ts; e[1] = tt;
+            if (m == 0) e[0] = 0.0;
+            if (m == 1) e[0] = 1.0;
+            if (m == 2) e[1] = 0.0;
+            if (m == 3) e[1] = 1.0;
+            return edge_of[m];
+        }
+    }
+    return -1;
+}
+
 /* -------------------------------------------------------------- one path -- */
 /* Runs path `path` from (s0,t0).  Returns the score F = (f, g) at the exit
  * point; *steps = Euler-Maruyama updates performed; *tie = 1 if any post-step
@@ -240,7 +287,7 @@ static int nearest_side(double s, double t, double e[2])
  * could flip); *capped = 1 if max_steps was reached without an exit. */
 void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
                  const double* edges, int family, int coef_mode, const double* p,
-                 uint64_t seed, double dt, uint64_t max_steps, double tie_delta,
+                 uint64_t seed, double dt, uint64_t max_steps, double tie_delta, int exit_test,
                  double F[2], uint64_t* steps, int* tie, int* capped)
 {
     double xs = s0, xt = t0;
@@ -264,6 +311,11 @@ void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
             flag = 1;
         edge = oracle_exit_point(xs, xt, ys, yt, e);
         if (edge >= 0) break;
+        if (exit_test == 1) {
+            edge = oracle_bridge_exit(xs, xt, ys, yt, dt, seed, node, path, (uint32_t)(k - 1), e,
+                                      &flag);
+            if (edge >= 0) break;
+        }
         xs = ys;
         xt = yt;
     }
@@ -287,7 +339,7 @@ void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
 void oracle_mc_node(int n, int i, int j, uint32_t node, const double* edges,
                     int family, int coef_mode, const double* p, uint64_t seed,
                     uint64_t path_begin, uint64_t path_end, double dt,
-                    uint64_t max_steps, double tie_delta,
+                    uint64_t max_steps, double tie_delta, int exit_test,
                     double sums[8], uint64_t counts[4])
 {
     double s0 = (double)i / (double)(n - 1);
@@ -300,7 +352,7 @@ void oracle_mc_node(int n, int i, int j, uint32_t node, const double* edges,
         uint64_t st;
         int tie, capped;
         oracle_path(n, s0, t0, node, (uint32_t)q, edges, family, coef_mode, p, seed,
-                    dt, max_steps, tie_delta, F, &st, &tie, &capped);
+                    dt, max_steps, tie_delta, exit_test, F, &st, &tie, &capped);
         for (int c = 0; c < 2; ++c) {
             double d = F[c] - x0[c];
             sums[0 + c] += d;

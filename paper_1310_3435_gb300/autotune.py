@@ -11,10 +11,11 @@ in a JSON file:
 Each candidate is timed with CUDA events on the real kernels, through the C
 ABI, on a reduced copy of the request: its first `probe_paths` paths per
 node for the Monte Carlo, and the full subdomain solves.  The fastest
-candidate wins.  Every candidate computes the same results: Monte Carlo sums
-are exact per work item in FP32 stepping and compensated across items, and a
-solve does not depend on its CTA size.  So tuning never changes results
-beyond the last bits of a compensated FP64 sum.
+candidate wins.  The Monte Carlo estimate does not depend on the work-item
+size beyond the last bits of a compensated FP64 sum (FP32-stepping sums are
+exact per item).  The CG solves reduce their dot products over the CTA's
+threads, so meshes from different CTA sizes agree to the solver tolerance
+rather than bit for bit.
 """
 from __future__ import annotations
 

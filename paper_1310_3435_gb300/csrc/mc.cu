@@ -329,6 +329,42 @@ __device__ __forceinline__ int nearest_edge(R s, R t, R& tau)
     return e;
 }
 
+// Brownian-bridge exit test of a step x -> y that ended inside (§2.2, after
+// Gobet): side m is crossed with probability p_m = exp(-d_m(x) d_m(y) / dt)
+// (noise sqrt(2) dW), decided by U_m of Philox counter (k, path, node, 1) in
+// the side order s=0, s=1, t=0, t=1 (edges 2, 3, 0, 1).  No side can be
+// crossed when every product is >= qmax = 23 dt (p < 2^-33), and then no
+// uniforms are drawn.  Returns the edge and the tangential coordinate of the
+// exit point (mean of the step's two), or -1.
+template <typename R, class Keys>
+__device__ __noinline__ int bridge_exit(R xs, R xt, R ys, R yt, R inv_dt, R qmax, const Keys& philox,
+                                        uint32_t k, uint32_t path, uint32_t node, R& tau, bool& tie)
+{
+    const R q[4] = {xs * ys, (R(1) - xs) * (R(1) - ys), xt * yt, (R(1) - xt) * (R(1) - yt)};
+    if (!((q[0] < qmax) | (q[1] < qmax) | (q[2] < qmax) | (q[3] < qmax))) return -1;
+    const uint4 r4 = philox(make_uint4(k, path, node, 1u));
+    const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (!(q[m] < qmax)) continue;
+        R p, u;
+        if constexpr (sizeof(R) == 8) {
+            p = exp(-q[m] * inv_dt);
+            u = ((double)rr[m] + 0.5) * 0x1p-32;
+            if (fabs(u - p) < 1e-12) tie = true;
+        } else {
+            p = ex2_approx(-q[m] * inv_dt * 1.44269504088896340736f);
+            u = uniform23(rr[m]);
+        }
+        if (u < p) {
+            tau = m < 2 ? fmin(fmax(R(0.5) * (xt + yt), R(0)), R(1))
+                        : fmin(fmax(R(0.5) * (xs + ys), R(0)), R(1));
+            return m == 0 ? 2 : m == 1 ? 3 : m == 2 ? 0 : 1;
+        }
+    }
+    return -1;
+}
+
 // Linear interpolation in a table of n values at tau_j = j/(n-1), in FP64.
 __device__ __forceinline__ double lookup(const double* __restrict__ T, int n, double tau)
 {
@@ -484,8 +520,14 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
     acc_zero(A, tid);
     __syncwarp();
 
+    const bool bridge = M.bridge != 0;
+    const R inv_dt = R(1) / dtR, qmax = R(23) * dtR;
+    int bedge = -1;
+    R btau = R(0);
+
     // One Euler-Maruyama step from (xs, xt) with normals (za, zb) into
-    // (ys, yt).  Returns 0 to continue, 1 on exit, 2 at the step cap.
+    // (ys, yt).  Returns 0 to continue, 1 on exit through the end point, 2 at
+    // the step cap, 3 on a Brownian-bridge crossing (edge bedge, btau).
     auto step = [&](R za, R zb, bool check_cap) -> int {
         R bs, bt;
         dens.drift(xs, xt, bs, bt);
@@ -497,6 +539,10 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
             tie = tie || (m < delta);
         }
         if ((ys <= R(0)) | (ys >= R(1)) | (yt <= R(0)) | (yt >= R(1))) return 1;
+        if (bridge) {
+            bedge = bridge_exit<R>(xs, xt, ys, yt, inv_dt, qmax, philox, k - 1u, path, node, btau, tie);
+            if (bedge >= 0) return 3;
+        }
         if (check_cap && k >= kmax) return 2;
         xs = ys;
         xt = yt;
@@ -775,6 +821,9 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     __syncwarp();
 
     const float c4dt = (float)(-4.0 * M.dt * 0.69314718055994530942);
+    const bool bridge = M.bridge != 0;
+    const float inv_dt = (float)(1.0 / M.dt), qmax = (float)(23.0 * M.dt);
+    const float dth = (float)std::sqrt(23.0 * M.dt);
     float xs = 0.f, xt = 0.f;
     uint32_t k = 0, path = 0, node = 0;
     int set = 0;
@@ -822,37 +871,47 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
             const float y1s = fmaf(na, ca, as), y1t = fmaf(na, sa, at);
             dens.advance(y1s, y1t, as, at);
             const float y2s = fmaf(nb, cb, as), y2t = fmaf(nb, sb, at);
-            // one test for both steps: every coordinate inside (0,1)?
+            // one test for both steps: every coordinate inside (0,1), and, with
+            // the bridge test, every coordinate of x, y1, y2 farther than
+            // sqrt(23 dt) from the sides (no crossing probability to draw)?
             const float lo = fminf(fminf(y1s, y1t), fminf(y2s, y2t));
             const float hi = fmaxf(fmaxf(y1s, y1t), fmaxf(y2s, y2t));
-            const bool out1 = (y1s <= 0.f) | (y1s >= 1.f) | (y1t <= 0.f) | (y1t >= 1.f);
-            const bool out2 = (y2s <= 0.f) | (y2s >= 1.f) | (y2t <= 0.f) | (y2t >= 1.f);
-            if ((lo > 0.f) & (hi < 1.f) && k + 2u < kmax) {
+            bool fast = (lo > 0.f) & (hi < 1.f) & (k + 2u < kmax);
+            if (bridge)
+                fast = fast & (fminf(lo, fminf(xs, xt)) >= dth) & (fmaxf(hi, fmaxf(xs, xt)) <= 1.f - dth);
+            if (fast) {
                 xs = y2s;
                 xt = y2t;
                 k += 2u;
             } else {
-                // exit or step cap within this pair (rare)
+                // exit, bridge crossing or step cap within this pair (rare)
                 float ps = xs, pt = xt, qs = y1s, qt = y1t;   // the step that ended
-                bool out = out1, capped = false;
+                float tau = 0.f;
+                bool capped = false, dummy = false;
+                int e = -1;
                 k += 1u;
-                if (!out1) {
-                    if (k >= kmax) {
+                const bool out1 = (y1s <= 0.f) | (y1s >= 1.f) | (y1t <= 0.f) | (y1t >= 1.f);
+                if (out1) {
+                    e = exit_edge<float>(xs, xt, y1s, y1t, tau);
+                } else if (bridge && (e = bridge_exit<float>(xs, xt, y1s, y1t, inv_dt, qmax, philox,
+                                                              k - 1u, path, node, tau, dummy)) >= 0) {
+                } else if (k >= kmax) {
+                    capped = true;
+                } else {
+                    ps = y1s; pt = y1t; qs = y2s; qt = y2t;
+                    k += 1u;
+                    const bool out2 = (y2s <= 0.f) | (y2s >= 1.f) | (y2t <= 0.f) | (y2t >= 1.f);
+                    if (out2) {
+                        e = exit_edge<float>(y1s, y1t, y2s, y2t, tau);
+                    } else if (bridge && (e = bridge_exit<float>(y1s, y1t, y2s, y2t, inv_dt, qmax,
+                                                                  philox, k - 1u, path, node, tau,
+                                                                  dummy)) >= 0) {
+                    } else if (k >= kmax) {
                         capped = true;
-                    } else {
-                        ps = y1s; pt = y1t; qs = y2s; qt = y2t;
-                        out = out2;
-                        k += 1u;
-                        capped = !out2 && k >= kmax;
                     }
                 }
-                if (out | capped) {
-                    float tau;
-                    int e = out ? exit_edge<float>(ps, pt, qs, qt, tau) : -1;
-                    if (e < 0) {                    // step cap (or a non-finite position)
-                        e = nearest_edge<float>(qs, qt, tau);
-                        capped = true;
-                    }
+                if (e >= 0 || capped) {
+                    if (e < 0) e = nearest_edge<float>(qs, qt, tau);
                     const int2 ij = M.nodes[node];
                     const double td = (double)tau;
                     const double d0 = lookup(M.edges + (size_t)e * n, n, td) - (double)ij.x * invd;
@@ -867,9 +926,10 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                     active = false;
                     ended = true;
                 } else {
-                    xs = y2s;                       // k + 2 == kmax reached without exit: next pair caps
+                    xs = y2s;                       // both steps stayed inside
                     xt = y2t;
                 }
+                (void)ps; (void)pt;
             }
         }
         dm = __ballot_sync(FULL, ended);

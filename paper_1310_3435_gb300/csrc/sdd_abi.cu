@@ -274,6 +274,8 @@ int validate_mc(const sdd_mc_params* mc)
         return fail(SDD_ERR_INVALID_ARG, "unknown precision");
     if (mc->chunk < 0 || mc->chunk > 8192 || (mc->chunk > 0 && mc->chunk % 32 != 0))
         return fail(SDD_ERR_INVALID_ARG, "chunk must be 0 or a multiple of 32 up to 8192");
+    if (mc->exit_test != SDD_EXIT_END_OF_STEP && mc->exit_test != SDD_EXIT_BRIDGE)
+        return fail(SDD_ERR_INVALID_ARG, "unknown exit_test");
     const double cap = mc->max_steps ? (double)mc->max_steps : std::ceil(2.0 / mc->dt);
     if (cap < 1.0 || cap > 4294967294.0)
         return fail(SDD_ERR_INVALID_ARG, "max_steps must be in [1, 2^32 - 2]");
@@ -300,6 +302,7 @@ void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
     m.chunk = chunk;
     m.chunks_per_node = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
     m.max_steps = (uint32_t)(mc->max_steps ? mc->max_steps : (uint64_t)std::ceil(2.0 / mc->dt));
+    m.bridge = mc->exit_test == SDD_EXIT_BRIDGE ? 1 : 0;
     m.n_nodes = p->n_nodes;
     m.dt = mc->dt;
     m.sqrt2dt = std::sqrt(2.0 * mc->dt);

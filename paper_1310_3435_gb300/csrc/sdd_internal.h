@@ -47,6 +47,8 @@ struct MeshDev {
     uint32_t chunk;         // paths per work item
     uint32_t chunks_per_node;
     uint32_t max_steps;     // step cap per path (< 2^32)
+    int32_t bridge;         // 1: Brownian-bridge exit test after each step
+    int32_t pad0;
     int64_t n_nodes;
     uint64_t item_begin;    // first work item of this mesh
     uint64_t node_begin;    // first global node of this mesh

@@ -33,6 +33,7 @@ SDD_COEF_W, SDD_COEF_INV_W = 0, 1
 SDD_BMAP_IDENTITY, SDD_BMAP_PAPER_1D, SDD_BMAP_TABLE = 0, 1, 2
 SDD_FP64, SDD_FP32_STEP = 0, 1
 SDD_SOLVER_SOR, SDD_SOLVER_CG_FP32_REFINE = 0, 1
+SDD_EXIT_END_OF_STEP, SDD_EXIT_BRIDGE = 0, 1
 
 
 class SddError(RuntimeError):
@@ -56,7 +57,8 @@ class sdd_mc_params(ctypes.Structure):
     _fields_ = [("paths_per_node", ctypes.c_uint64), ("dt", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("max_steps", ctypes.c_uint64),
-                ("tie_delta", ctypes.c_double)]
+                ("tie_delta", ctypes.c_double), ("exit_test", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class sdd_mc_stats(ctypes.Structure):
@@ -238,7 +240,8 @@ def sdd_plan_edges(plan, n: int) -> np.ndarray:
 
 
 def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, chunk: int = 0,
-              max_steps: int = 0, tie_delta: float = -1.0) -> sdd_mc_params:
+              max_steps: int = 0, tie_delta: float = -1.0,
+              exit_test: int = SDD_EXIT_END_OF_STEP) -> sdd_mc_params:
     m = sdd_mc_params()
     m.paths_per_node = int(paths)
     m.dt = float(dt)
@@ -247,6 +250,7 @@ def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, c
     m.chunk = int(chunk)
     m.max_steps = int(max_steps)
     m.tie_delta = float(tie_delta)
+    m.exit_test = int(exit_test)
     return m
 
 
@@ -387,7 +391,8 @@ class Plan:
     def mc_params(self, **kw) -> sdd_mc_params:
         s = self.spec
         args = dict(paths=s.paths, dt=s.dt, seed=s.seed, precision=s.precision,
-                    max_steps=s.max_steps, tie_delta=s.tie_delta)
+                    max_steps=s.max_steps, tie_delta=s.tie_delta,
+                    exit_test=getattr(s, "exit_test", SDD_EXIT_END_OF_STEP))
         args.update(kw)
         return mc_params(**args)
 

@@ -110,4 +110,6 @@ def test_autotuned_parameters_are_valid_and_keep_results(tmp_path):
         N.sdd_mesh_generate(P.handle, P.mc_params(chunk=pick["chunk"]),
                             P.solve_params(block_threads=pick["block_threads"]), mesh, mean, se)
     assert np.allclose(mean, base[1], rtol=0, atol=1e-14)
-    assert np.allclose(mesh, base[0], rtol=0, atol=1e-12)
+    # CG dot products are reduced over the CTA's threads: meshes agree to the
+    # solve tolerance (relative residual 1e-10), not bit for bit
+    assert np.max(np.abs(mesh - base[0])) < 1e-8, np.max(np.abs(mesh - base[0]))

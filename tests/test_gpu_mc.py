@@ -173,3 +173,31 @@ def test_fp32_sums_are_exact_and_reproducible(orc):
             assert np.array_equal(c["paths"], a["paths"])
             assert np.allclose(c["sum"], a["sum"], rtol=1e-15, atol=1e-12)
             assert np.allclose(c["sumsq"], a["sumsq"], rtol=1e-15, atol=1e-12)
+
+
+@pytest.mark.parametrize("case", range(len(W.small_parity_cases())))
+def test_fp64_bridge_matches_oracle(orc, case):
+    """The Brownian-bridge exit test replays the oracle too (its uniforms come
+    from the same Philox streams, counter word 3 = 1)."""
+    spec = W.MeshSpec(**{**W.small_parity_cases()[case].__dict__, "exit_test": W.EXIT_BRIDGE})
+    nodes = orc.interface_nodes(spec.n, spec.sx, spec.sy)
+    g = gpu_sums(spec)
+    E = orc.bmap_tables(spec.n, spec.bmap_mode, spec.family, spec.coef_mode, spec.params)
+    o = orc.mc_nodes(spec.n, nodes, E, spec.family, spec.coef_mode, spec.params, seed=spec.seed,
+                     paths=spec.paths, dt=spec.dt, max_steps=spec.cap(), tie_delta=spec.tie(),
+                     exit_test=1)
+    _compare_fp64(orc, spec, g, o, nodes)
+    # the bridge ends paths earlier than the end-of-step test
+    g0 = gpu_sums(W.small_parity_cases()[case])
+    assert g["steps"].sum() < g0["steps"].sum()
+
+
+def test_fp32_bridge_paired_with_fp64(orc):
+    spec = W.MeshSpec(**{**W.small_parity_cases()[1].__dict__, "exit_test": W.EXIT_BRIDGE})
+    nodes = orc.interface_nodes(spec.n, spec.sx, spec.sy)
+    g64 = gpu_sums(spec, precision=W.FP64)
+    g32 = gpu_sums(spec, precision=W.FP32_STEP)
+    m64, se64 = gpu_means(g64, spec.n, nodes)
+    m32, _ = gpu_means(g32, spec.n, nodes)
+    assert np.all(np.abs(m32 - m64) <= se64)
+    assert abs(int(g32["steps"].sum()) - int(g64["steps"].sum())) / g64["steps"].sum() < 2e-3

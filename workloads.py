@@ -28,6 +28,7 @@ FAMILY_BUMPS, FAMILY_RING, FAMILY_RIDGE = 0, 1, 2
 COEF_W, COEF_INV_W = 0, 1
 BMAP_IDENTITY, BMAP_PAPER_1D, BMAP_TABLE = 0, 1, 2
 FP64, FP32_STEP = 0, 1
+EXIT_END_OF_STEP, EXIT_BRIDGE = 0, 1
 SOLVER_SOR, SOLVER_CG_FP32_REFINE = 0, 1
 
 
@@ -49,6 +50,7 @@ class MeshSpec:
     tie_delta: float = -1.0      # <0: default (1e-11 in FP64 stepping, 0 in FP32)
     solver: int = SOLVER_SOR
     tol: float = 1e-10
+    exit_test: int = EXIT_END_OF_STEP
     label: str = ""
 
     def cap(self) -> int:
