@@ -570,8 +570,8 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
                 if (!ended) ended = step(z2, z3, true);
             }
             if (ended) {
-                R tau;
-                int e = ended == 1 ? exit_edge<R>(xs, xt, ys, yt, tau) : -1;
+                R tau = btau;                      // bridge crossing: edge and point known
+                int e = ended == 1 ? exit_edge<R>(xs, xt, ys, yt, tau) : ended == 3 ? bedge : -1;
                 if (e < 0) {                       // step cap (or a non-finite position)
                     e = nearest_edge<R>(ys, yt, tau);
                     ended = 2;
