@@ -3,8 +3,10 @@
 Two choices are tuned, each per bucket of similar requests and cached per GPU
 in a JSON file:
 
-* paths per work item (`chunk`) of the interface Monte Carlo, bucketed by
-  (precision, density family, log2 of interface nodes x paths per node);
+* paths per work item (`chunk`) of the interface Monte Carlo in FP64
+  stepping, bucketed by (density family, log2 of interface nodes x paths per
+  node).  FP32 stepping keeps the automatic size: its lanes stream across work
+  items, and its speed does not depend on the item size (measured);
 * threads per subdomain CTA of the batched solves (256, 512, 1024), bucketed
   by (solver, log2 of the largest subdomain's interior nodes).
 
@@ -127,6 +129,8 @@ class Autotuner:
         if n_nodes is None:
             n_nodes = (spec.sx - 1) * (spec.n - 2) + (spec.sy - 1) * (spec.n - 2) - (
                 spec.sx - 1) * (spec.sy - 1)
-        chunk = self._best(mc_bucket(spec, n_nodes), "mc", spec, CHUNKS)
+        chunk = 0
+        if int(spec.precision) == 0:                  # FP64 stepping: item-at-a-time lanes
+            chunk = self._best(mc_bucket(spec, n_nodes), "mc", spec, CHUNKS)
         threads = self._best(solve_bucket(spec), "solve", spec, SOLVE_THREADS)
         return {"chunk": int(chunk), "block_threads": int(threads)}

@@ -15,9 +15,13 @@ def test_picks_fastest_and_caches(tmp_path):
 
     path = str(tmp_path / "tune.json")
     t = A.Autotuner(timer=timer, device_name="fake", path=path)
-    spec = W.config3(count=1)[0]
+    spec = W.config3(count=1, precision=W.FP64)[0]
     got = t.tune(spec)
     assert got == {"chunk": 1024, "block_threads": 512}
+    assert len(calls) == 6
+    # FP32 stepping keeps the automatic work-item size; only the solve is tuned
+    spec32 = W.config3(count=1)[0]
+    assert t.tune(spec32) == {"chunk": 0, "block_threads": 512}
     assert len(calls) == 6
     t.save()
     t2 = A.Autotuner(timer=timer, device_name="fake", path=path)
