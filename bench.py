@@ -198,7 +198,8 @@ def run_native(args):
     dev = torch.device("cuda", local)
     spec = make_spec(args.config)
     # independent problem per rank: its own seed (weak scaling, no collective)
-    over = {"seed": spec.seed + 1000003 * rank}
+    from paper_1310_3435_gb300 import replicas
+    over = {"seed": replicas.rank_seed(spec.seed, rank)}
     if args.paths:
         over["paths"] = args.paths
     spec = W.MeshSpec(**{**spec.__dict__, **over})
@@ -255,12 +256,9 @@ def run_native(args):
     t_total = sum(ms_step) / 1000.0
     check = N.sdd_plan_last_mc_stats(plan.handle)
     assert int(check.path_steps) == path_steps
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = world * path_steps * args.steps / t_total
-    meshes_per_s = world * args.steps / t_total
+    t_total = replicas.max_over_ranks(t_total, device=dev)
+    value = replicas.whole_job_rate(path_steps * args.steps, world, t_total)
+    meshes_per_s = replicas.whole_job_rate(args.steps, world, t_total)
 
     # end to end through the public API with host buffers: plan (H2D of the
     # request's tables) + mesh generation + D2H of mesh and interface values
