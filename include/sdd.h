@@ -264,6 +264,33 @@ int sdd_batch_plan_stats(sdd_batch* batch, int index, sdd_mc_stats* mc, sdd_solv
 /* Frees the batch (not its plans). */
 void sdd_batch_destroy(sdd_batch* batch);
 
+/* Allocation-free interface Monte Carlo, for callers that cannot allocate
+ * device memory: code running under an allocator owned by someone else (a
+ * framework's caching allocator, an embedded runtime with a fixed budget) or
+ * at points where an allocation would synchronise or could fail.  The paper
+ * has no counterpart: this is a deployment variant of sdd_interface_mc.
+ * It needs no plan.  It runs the same path kernel and reduction as
+ * sdd_interface_mc, and its only scratch (work counter, counters, per-work-item
+ * sums) is one file-scope 8 MiB device array inside the library, which every
+ * GPU that loads the library keeps until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating routine.
+ * Inputs, all device memory owned by the caller: nodes int32 [n_nodes][2]
+ * (i, j), in the order whose index is the node's Philox counter word (the
+ * plans' order reproduces sdd_interface_mc); edges, the boundary tables
+ * [2][4][n].  Host inputs: dens, mc (as sdd_interface_mc).  Outputs, device
+ * memory: mean [n_nodes][2] (required), stderr_ [n_nodes][2] (may be NULL).
+ * Asynchronous on `stream`.
+ * Limit: n_nodes * ceil(N / chunk) work items must fit the array (55185);
+ * chunk = 0 picks the automatic size, raised up to 8192 until they fit;
+ * larger requests fail with SDD_ERR_INVALID_ARG and a message.
+ * The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_nodes, const double* edges,
+                            const sdd_density* dens, const sdd_mc_params* mc, double* mean,
+                            double* stderr_, void* stream);
+
 /* Frees the plan and its device buffers.  Memory is stream-ordered: the free
  * is queued on the plan's last stream after its work, and the call does not
  * synchronise.  A plan must outlive the batches that use it. */

@@ -1190,3 +1190,119 @@ int sdd_plan_results(sdd_plan* p, double* mesh, double* mean, double* stderr_, v
 }
 
 }  // extern "C"
+
+// ------------------------------------------- allocation-free Monte Carlo --
+// Some callers cannot allocate device memory: code that runs where the
+// allocator is owned by someone else (a framework's caching allocator, an
+// embedded runtime with a fixed memory budget) or where a cudaMalloc would
+// synchronise or fail at the wrong moment.  For them sdd_interface_mc_static
+// runs the same path kernel and reduction as sdd_interface_mc, with every byte
+// of its scratch (work counter, counters, per-work-item sums) in this
+// file-scope device array.  Every GPU that loads the library holds the array
+// until the process exits.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;            // 8 MiB
+constexpr size_t kStaticHeadBytes = 512;                           // counter + stats
+constexpr uint64_t kStaticMaxItems = (kStaticScratchBytes - kStaticHeadBytes) / sizeof(Slot);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_ptr[64] = {};
+
+// Device address of the array for the current device: looked up once per
+// device (the first call on a device), with that device current.
+int static_scratch(void** out)
+{
+    int dev = -1;
+    SDD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SDD_ERR_NO_DEVICE, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return SDD_OK;
+}
+
+}  // namespace
+
+extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_nodes,
+                                       const double* edges, const sdd_density* dens,
+                                       const sdd_mc_params* mc, double* mean, double* stderr_,
+                                       void* stream_)
+{
+    clear_error();
+    if (n < 3 || n > 16385) return fail(SDD_ERR_INVALID_ARG, "n must be in [3, 16385]");
+    if (n_nodes < 1) return fail(SDD_ERR_INVALID_ARG, "n_nodes must be >= 1");
+    if (!nodes || !edges || !mean)
+        return fail(SDD_ERR_INVALID_ARG, "nodes, edges and mean are required");
+    int rc = validate_density(dens);
+    if (rc) return rc;
+    if ((rc = validate_mc(mc))) return rc;
+    if (!is_device_ptr(nodes) || !is_device_ptr(edges) || !is_device_ptr(mean) ||
+        (stderr_ && !is_device_ptr(stderr_)))
+        return fail(SDD_ERR_INVALID_ARG, "nodes, edges, mean and stderr_ must be device memory");
+    // work-item size: the caller's, else the automatic one, raised (up to 8192
+    // paths) until the work items fit the static array
+    uint32_t chunk = mc->chunk ? (uint32_t)mc->chunk : auto_chunk(mc->paths_per_node, n_nodes);
+    auto items_for = [&](uint32_t c) {
+        return (uint64_t)n_nodes * ((mc->paths_per_node + c - 1) / c);
+    };
+    if (!mc->chunk)
+        while (items_for(chunk) > kStaticMaxItems && chunk < 8192) chunk *= 2;
+    chunk = std::min<uint32_t>(chunk, 8192);
+    const uint64_t items = items_for(chunk);
+    if (items > kStaticMaxItems)
+        return fail(SDD_ERR_INVALID_ARG,
+                    "too much work for the static scratch: n_nodes * ceil(N / chunk) = " +
+                        std::to_string(items) + " work items, at most " +
+                        std::to_string(kStaticMaxItems) + " fit in 8 MiB");
+    void* base = nullptr;
+    if ((rc = static_scratch(&base))) return rc;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    cudaStream_t stream = as_stream(stream_);
+
+    McArgs a;
+    memset(&a, 0, sizeof(a));
+    MeshDev& m = a.single;
+    m.n = n;
+    m.family = dens->family;
+    m.precision = mc->precision;
+    m.key0 = (uint32_t)(mc->seed & 0xffffffffu);
+    m.key1 = (uint32_t)(mc->seed >> 32);
+    m.paths = (uint32_t)mc->paths_per_node;
+    m.chunk = chunk;
+    m.chunks_per_node = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
+    m.max_steps = (uint32_t)(mc->max_steps ? mc->max_steps : (uint64_t)std::ceil(2.0 / mc->dt));
+    m.bridge = mc->exit_test == SDD_EXIT_BRIDGE ? 1 : 0;
+    m.n_nodes = n_nodes;
+    m.dt = mc->dt;
+    m.sqrt2dt = std::sqrt(2.0 * mc->dt);
+    m.tie_delta = mc->tie_delta >= 0.0 ? mc->tie_delta : (mc->precision == SDD_FP64 ? 1e-11 : 0.0);
+    m.nodes = reinterpret_cast<const int2*>(nodes);
+    m.edges = edges;
+    m.sums = nullptr;
+    m.mean = mean;
+    m.stderr_ = stderr_;
+    m.stats = reinterpret_cast<McStatsDev*>(b + 256);
+    sdd_density d = *dens;
+    for (int q = d.n_params; q < SDD_MAX_PARAMS; ++q) d.params[q] = 0.0;
+    fill_fp32_params(m, d);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[2 * r] = m.key0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[2 * r + 1] = m.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    a.meshes = nullptr;
+    a.n_meshes = 1;
+    a.total_items = items;
+    a.total_nodes = (uint64_t)n_nodes;
+    a.queue = reinterpret_cast<unsigned long long*>(b);          // zeroed by the launcher
+    a.slots = reinterpret_cast<Slot*>(b + kStaticHeadBytes);     // written before read
+    SDD_CUDA(cudaMemsetAsync(m.stats, 0, sizeof(McStatsDev), stream));
+    return launch_mc(a, mc->precision, mesh_fam_class(m.family, m.nb), stream);
+}

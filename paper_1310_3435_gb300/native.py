@@ -148,11 +148,13 @@ def load(build_if_missing: bool = True):
     L.sdd_batch_plan_stats.argtypes = [vp, ctypes.c_int, P(sdd_mc_stats), P(sdd_solve_stats)]
     L.sdd_batch_destroy.argtypes = [vp]
     L.sdd_batch_destroy.restype = None
+    L.sdd_interface_mc_static.argtypes = [ctypes.c_int, vp, ctypes.c_int64, vp, P(sdd_density),
+                                          P(sdd_mc_params), vp, vp, vp]
     for name in ("sdd_mesh_plan", "sdd_plan_num_nodes", "sdd_plan_nodes", "sdd_plan_edges",
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
                  "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
                  "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
-                 "sdd_batch_plan_stats"):
+                 "sdd_batch_plan_stats", "sdd_interface_mc_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -350,6 +352,17 @@ def sdd_batch_plan_stats(batch, index: int, allow_not_converged: bool = False):
 def sdd_batch_destroy(batch) -> None:
     if batch:
         load().sdd_batch_destroy(batch)
+
+
+def sdd_interface_mc_static(n: int, nodes, edges, density: sdd_density, mc: sdd_mc_params,
+                            mean, stderr=None, stream=None) -> None:
+    """Allocation-free interface Monte Carlo (see include/sdd.h): device
+    arrays nodes int32 [n_nodes][2], edges [2][4][n], mean/stderr [n_nodes][2]."""
+    n_nodes = int(nodes.shape[0]) if hasattr(nodes, "shape") else 0
+    _check(load().sdd_interface_mc_static(int(n), _ptr(nodes), n_nodes, _ptr(edges),
+                                          ctypes.byref(density), ctypes.byref(mc), _ptr(mean),
+                                          _ptr(stderr), _stream(stream)),
+           "sdd_interface_mc_static")
 
 
 def sdd_plan_destroy(plan) -> None:
