@@ -427,3 +427,129 @@ def torsion_exit_time(s: float, t: float, terms: int = 401) -> float:
     terms_ = 16.0 * np.sin(M * math.pi * s) * np.sin(K * math.pi * t) / (
         math.pi ** 4 * M * K * (M * M + K * K))
     return float(terms_.sum())
+
+
+# ------------------------------------------------------- mesh quality -----
+def cell_quality(U: np.ndarray) -> np.ndarray:
+    """Geometric quality Q(K) = 1/2 tr(J^T J) / sqrt(det(J^T J)) of every cell
+    K of a mesh U[j, i, comp] (eq. Qmeasure, §3.1).  J is the Jacobian of the
+    map (s, t) -> u on the cell, from the mean of the cell's two edge
+    differences in each direction.  Q >= 1, Q = 1 for a square cell; inf for a
+    folded cell (det J <= 0).  Shape [n-1, n-1]."""
+    n = U.shape[0]
+    h = 1.0 / (n - 1)
+    du_ds = ((U[:-1, 1:] - U[:-1, :-1]) + (U[1:, 1:] - U[1:, :-1])) / (2 * h)
+    du_dt = ((U[1:, :-1] - U[:-1, :-1]) + (U[1:, 1:] - U[:-1, 1:])) / (2 * h)
+    a, c = du_ds[..., 0], du_ds[..., 1]          # J = [[a, b], [c, d]]
+    b, d = du_dt[..., 0], du_dt[..., 1]
+    det = a * d - b * c
+    fro = a * a + b * b + c * c + d * d
+    with np.errstate(divide="ignore", invalid="ignore"):
+        q = np.where(det > 0, 0.5 * fro / np.where(det > 0, det, 1.0), np.inf)
+    return q
+
+
+def mesh_quality(U: np.ndarray, ref: np.ndarray | None = None, family: int = 0,
+                 coef_mode: int = 0, params=(0.0,)) -> dict:
+    """Q_max, Q_mean and folded cells of U; with a reference mesh also
+    R_max = Q_max(ref)/Q_max(U), R_mean = Q_mean(ref)/Q_mean(U) and
+    l_inf = max over nodes |rho(U) - rho(ref)|, rho = w (the mesh density)
+    evaluated at the mesh points (§3.3)."""
+    q = cell_quality(U)
+    ok = np.isfinite(q)
+    out = {"q_max": float(q[ok].max()) if ok.any() else math.inf,
+           "q_mean": float(q[ok].mean()) if ok.any() else math.inf,
+           "folds": int((~ok).sum())}
+    if ref is not None:
+        qr = cell_quality(ref)
+        out["r_max"] = float(qr[np.isfinite(qr)].max() / out["q_max"])
+        out["r_mean"] = float(qr[np.isfinite(qr)].mean() / out["q_mean"])
+        c_u = coef(family, 0, params, U[..., 0], U[..., 1])
+        c_r = coef(family, 0, params, ref[..., 0], ref[..., 1])
+        out["l_inf"] = float(np.abs(c_u - c_r).max())
+    return out
+
+
+# ----------------------------------------------- few-point interfaces -----
+def line_nodes(n: int, sx: int, sy: int) -> list:
+    """Interface lines as lists of grid nodes, boundary endpoints included:
+    ('v', i, [(i, j) for j = 0..n-1]) for each vertical line i in I_x and
+    ('h', j, [(i, j) for i = 0..n-1]) for each horizontal line."""
+    out = [("v", i, [(i, j) for j in range(n)]) for i in interface_indices(n, sx)]
+    out += [("h", j, [(i, j) for i in range(n)]) for j in interface_indices(n, sy)]
+    return out
+
+
+def placement(n: int, sx: int, sy: int, mode: int, k: int = 7, family: int = 0,
+              params=(0.0,)) -> np.ndarray:
+    """Boolean mask over interface_nodes(n, sx, sy): the nodes where the Monte
+    Carlo estimate is computed (§3.6).  Crossings of two lines are always
+    included.  mode 0: every node; 1: k equispaced points per line
+    (positions round(m (n-1)/(k+1)), m = 1..k); 2: the local extrema, along
+    each line, of the first and second derivative of the density rho = w in
+    the line's direction (centred differences of w at the line's nodes)."""
+    nodes = interface_nodes(n, sx, sy)
+    index = {(int(i), int(j)): q for q, (i, j) in enumerate(nodes)}
+    mask = np.zeros(len(nodes), dtype=bool)
+    if mode == 0:
+        mask[:] = True
+        return mask
+    ix, iy = set(interface_indices(n, sx)), set(interface_indices(n, sy))
+    for q, (i, j) in enumerate(nodes):
+        if i in ix and j in iy:
+            mask[q] = True
+    h = 1.0 / (n - 1)
+    for kind, _, pts in line_nodes(n, sx, sy):
+        m = len(pts)
+        if mode == 1:
+            chosen = [int((2 * r * (m - 1) + (k + 1)) // (2 * (k + 1))) for r in range(1, k + 1)]
+        else:
+            s = np.array([p[0] for p in pts], dtype=np.float64) * h
+            t = np.array([p[1] for p in pts], dtype=np.float64) * h
+            rho = coef(family, 0, params, s, t)
+            d1 = np.zeros(m)
+            d2 = np.zeros(m)
+            d1[1:-1] = (rho[2:] - rho[:-2]) / (2 * h)
+            d2[1:-1] = (rho[2:] - 2 * rho[1:-1] + rho[:-2]) / (h * h)
+            chosen = []
+            for d in (d1, d2):
+                for r in range(2, m - 2):
+                    if (d[r] > d[r - 1] and d[r] >= d[r + 1]) or (d[r] < d[r - 1] and d[r] <= d[r + 1]):
+                        chosen.append(r)
+        for r in chosen:
+            if 1 <= r <= m - 2:
+                q = index.get(pts[r])
+                if q is not None:
+                    mask[q] = True
+    return mask
+
+
+def interpolate_interface(n: int, sx: int, sy: int, edges: np.ndarray, mask: np.ndarray,
+                          values: np.ndarray) -> np.ndarray:
+    """Fills every interface node from the values at the masked nodes by
+    linear interpolation along its line, the line's boundary endpoints taking
+    the boundary map (§3.6).  values: [n_nodes, 2] (rows of unmasked nodes
+    ignored).  Vertical lines first, so crossings (always masked) and
+    horizontal-line nodes never conflict."""
+    nodes = interface_nodes(n, sx, sy)
+    index = {(int(i), int(j)): q for q, (i, j) in enumerate(nodes)}
+    U = boundary_grid(n, edges)
+    out = np.array(values, dtype=np.float64).copy()
+    for kind, _, pts in line_nodes(n, sx, sy):
+        known_r, known_v = [], []
+        for r, p in enumerate(pts):
+            if r == 0 or r == len(pts) - 1:
+                known_r.append(r)
+                known_v.append(U[p[1], p[0]])
+            else:
+                q = index[p]
+                if mask[q]:
+                    known_r.append(r)
+                    known_v.append(values[q])
+        known_v = np.array(known_v)
+        for r, p in enumerate(pts[1:-1], start=1):
+            q = index[p]
+            if not mask[q]:
+                for c in range(2):
+                    out[q, c] = np.interp(r, known_r, known_v[:, c])
+    return out
