@@ -99,6 +99,19 @@ extern "C" {
 #define SDD_EXIT_END_OF_STEP 0
 #define SDD_EXIT_BRIDGE      1
 
+/* few-point interface (§3.6): where the Monte Carlo estimate is computed; the
+ * other interface nodes are interpolated linearly along their interface line
+ * between the nearest Monte Carlo nodes or the line's boundary ends
+ *   ALL        : every interface node (default)
+ *   EQUISPACED : k equispaced points per interface line, positions
+ *                round(r (n-1)/(k+1)), r = 1..k
+ *   EXTREMA    : the nodes where the first or the second centred difference
+ *                of the density w along the line has a local extremum
+ * Crossings of two interface lines are always Monte Carlo nodes. */
+#define SDD_PLACE_ALL        0
+#define SDD_PLACE_EQUISPACED 1
+#define SDD_PLACE_EXTREMA    2
+
 /* subdomain solvers */
 #define SDD_SOLVER_SOR            0   /* FP64 red-black SOR */
 #define SDD_SOLVER_CG_FP32_REFINE 1   /* FP32 Jacobi-PCG inner solves + FP64 iterative refinement */
@@ -225,6 +238,37 @@ int sdd_subdomain_solve(sdd_plan* plan, const double* iface, const sdd_solve_par
 int sdd_mesh_generate(sdd_plan* plan, const sdd_mc_params* mc, const sdd_solve_params* sp,
                       double* mesh, double* iface_mean, double* iface_stderr,
                       sdd_mc_stats* mc_stats, sdd_solve_stats* solve_stats, void* stream);
+
+/* Chooses the plan's Monte Carlo nodes (SDD_PLACE_*; k: points per line for
+ * EQUISPACED).  The Monte Carlo then runs on those nodes only, each with its
+ * Philox counter word of the full interface list (so its estimate equals the
+ * full run's), and the other interface nodes are interpolated (their std-err
+ * too).  Outputs keep the full [n_nodes] layout; node sums of interpolated
+ * nodes are zero.  Paper: §3.6.  Errors: INVALID_ARG, OOM, CUDA. */
+int sdd_plan_set_placement(sdd_plan* plan, int mode, int k);
+
+/* The placement: mask [n_nodes] (1 = Monte Carlo node, host) and the count
+ * of Monte Carlo nodes (either may be NULL). */
+int sdd_plan_placement(const sdd_plan* plan, uint8_t* mask, int64_t* n_mc);
+
+/* Mesh quality (§3.1 eq. Qmeasure, §3.3): per cell K of the computational
+ * grid, Q(K) = 1/2 tr(J^T J) / sqrt(det(J^T J)) with J the Jacobian of
+ * (s,t) -> u from the cell's edge differences (>= 1; a cell with det J <= 0
+ * is folded and left out of max and mean).  With a reference mesh (e.g. the
+ * single-domain mesh) also R_max = Q_max(ref)/Q_max, R_mean =
+ * Q_mean(ref)/Q_mean and l_inf = max over nodes |w(u) - w(ref)|. */
+typedef struct {
+    double q_max, q_mean;
+    int64_t folds;
+    double ref_q_max, ref_q_mean;
+    int64_t ref_folds;
+    double r_max, r_mean, l_inf;
+} sdd_quality;
+
+/* mesh, ref: [n][n][2], host or device (ref may be NULL); out: host.
+ * Synchronises `stream`. */
+int sdd_mesh_quality(sdd_plan* plan, const double* mesh, const double* ref, sdd_quality* out,
+                     void* stream);
 
 /* Copies the plan's last results: mesh [n][n][2] (after a solve), interface
  * means and standard errors [n_nodes][2] (after a Monte Carlo call or a batch

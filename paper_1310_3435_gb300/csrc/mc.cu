@@ -499,6 +499,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
     using R = typename RealOf<PREC>::T;
     const int n = M.n;
     const int2 ij = M.nodes[node];
+    const uint32_t nid = M.node_ids ? M.node_ids[node] : node;     // Philox counter word
     const double s0d = (double)ij.x / (double)(n - 1);
     const double t0d = (double)ij.y / (double)(n - 1);
     const R s0 = (R)s0d, t0 = (R)t0d;
@@ -540,7 +541,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
         }
         if ((ys <= R(0)) | (ys >= R(1)) | (yt <= R(0)) | (yt >= R(1))) return 1;
         if (bridge) {
-            bedge = bridge_exit<R>(xs, xt, ys, yt, inv_dt, qmax, philox, k - 1u, path, node, btau, tie);
+            bedge = bridge_exit<R>(xs, xt, ys, yt, inv_dt, qmax, philox, k - 1u, path, nid, btau, tie);
             if (bedge >= 0) return 3;
         }
         if (check_cap && k >= kmax) return 2;
@@ -552,7 +553,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
     for (;;) {
         int ended = 0;
         if (active) {
-            const uint4 r = philox(make_uint4(k >> 1, path, node, 0u));
+            const uint4 r = philox(make_uint4(k >> 1, path, nid, 0u));
             R z0, z1, z2, z3;
             if constexpr (PREC == SDD_FP64) {
                 box_muller_f64(r.x, r.y, z0, z1);
@@ -825,7 +826,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     const float inv_dt = (float)(1.0 / M.dt), qmax = (float)(23.0 * M.dt);
     const float dth = (float)std::sqrt(23.0 * M.dt);
     float xs = 0.f, xt = 0.f;
-    uint32_t k = 0, path = 0, node = 0;
+    uint32_t k = 0, path = 0, node = 0, nid = 0;
     int set = 0;
     bool active = false;
 
@@ -843,6 +844,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
             if ((rf.given >> lane) & 1u) {
                 path = rf.path;
                 node = rf.node;
+                nid = M.node_ids ? M.node_ids[node] : node;
                 set = rf.set;
                 const int2 ij = M.nodes[node];
                 xs = (float)ij.x * invf;
@@ -862,7 +864,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
         if (active) {
             // two Euler-Maruyama steps from one Philox block, both computed
             // before the exit tests (a step after an exit is discarded)
-            const uint4 r = philox(make_uint4(k >> 1, path, node, 0u));
+            const uint4 r = philox(make_uint4(k >> 1, path, nid, 0u));
             float na, ca, sa, nb, cb, sb;
             box_muller_f32_step(r.x, r.y, c4dt, na, ca, sa);
             box_muller_f32_step(r.z, r.w, c4dt, nb, cb, sb);
@@ -894,7 +896,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                 if (out1) {
                     e = exit_edge<float>(xs, xt, y1s, y1t, tau);
                 } else if (bridge && (e = bridge_exit<float>(xs, xt, y1s, y1t, inv_dt, qmax, philox,
-                                                              k - 1u, path, node, tau, dummy)) >= 0) {
+                                                              k - 1u, path, nid, tau, dummy)) >= 0) {
                 } else if (k >= kmax) {
                     capped = true;
                 } else {
@@ -904,7 +906,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                     if (out2) {
                         e = exit_edge<float>(y1s, y1t, y2s, y2t, tau);
                     } else if (bridge && (e = bridge_exit<float>(y1s, y1t, y2s, y2t, inv_dt, qmax,
-                                                                  philox, k - 1u, path, node, tau,
+                                                                  philox, k - 1u, path, nid, tau,
                                                                   dummy)) >= 0) {
                     } else if (k >= kmax) {
                         capped = true;
@@ -1102,6 +1104,7 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ McArgs a
     }
     const double N = (double)M.paths;
     const int2 ij = M.nodes[v];
+    const uint64_t vo = M.node_ids ? (uint64_t)M.node_ids[v] : v;   // output row
     const double x0[2] = {(double)ij.x / (double)(M.n - 1), (double)ij.y / (double)(M.n - 1)};
     sdd_node_sums out;
     double se_max = 0.0;
@@ -1117,14 +1120,14 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ McArgs a
         const double var = fmax(Q - S * S / N, 0.0) / (N * (N - 1.0));
         const double se = sqrt(var);
         se_max = fmax(se_max, se);
-        if (M.mean) M.mean[2 * v + q] = x0[q] + S / N;
-        if (M.stderr_) M.stderr_[2 * v + q] = se;
+        if (M.mean) M.mean[2 * vo + q] = x0[q] + S / N;
+        if (M.stderr_) M.stderr_[2 * vo + q] = se;
     }
     out.paths = paths;
     out.ties = ties;
     out.non_exits = caps;
     out.steps = steps;
-    if (M.sums) M.sums[v] = out;
+    if (M.sums) M.sums[vo] = out;
     atomicAdd(&M.stats->steps, steps);
     atomicAdd(&M.stats->ties, ties);
     atomicAdd(&M.stats->caps, caps);
@@ -1132,7 +1135,36 @@ __global__ void __launch_bounds__(256) k_reduce(const __grid_constant__ McArgs a
     atomicMax(&M.stats->max_stderr_bits, (unsigned long long)__double_as_longlong(se_max));
 }
 
+// Few-point interface: interpolated nodes from the Monte Carlo nodes (or the
+// boundary map) at both ends of their stretch of interface line.
+__global__ void k_interp(const InterpEntry* __restrict__ e, int64_t count)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    const InterpEntry E = e[g];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const double A = E.a >= 0 ? E.mean[2 * E.a + c] : E.ca[c];
+        const double B = E.b >= 0 ? E.mean[2 * E.b + c] : E.cb[c];
+        E.mean[2 * E.q + c] = (1.0 - E.w) * A + E.w * B;
+        if (E.se) {
+            const double sa = E.a >= 0 ? E.se[2 * E.a + c] : 0.0;
+            const double sb = E.b >= 0 ? E.se[2 * E.b + c] : 0.0;
+            E.se[2 * E.q + c] = (1.0 - E.w) * sa + E.w * sb;
+        }
+    }
+}
+
 }  // namespace
+
+int launch_interp(const InterpEntry* d_entries, int64_t count, cudaStream_t stream)
+{
+    if (count <= 0) return SDD_OK;
+    k_interp<<<(unsigned)((count + 255) / 256), 256, 0, stream>>>(d_entries, count);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
 
 // ------------------------------------------------------------ host side ----
 void fill_fp32_params(MeshDev& m, const sdd_density& d)

@@ -322,14 +322,26 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     memset(&a, 0, sizeof(a));
     MeshDev& m = a.single;
     mesh_record(p, mc, m);
-    const uint64_t items = (uint64_t)p->n_nodes * m.chunks_per_node;
+    const bool few = p->n_mc < p->n_nodes;            // few-point interface
+    if (few) {
+        m.n_nodes = p->n_mc;
+        if (m.chunk == auto_chunk(mc->paths_per_node, p->n_nodes) && !mc->chunk) {
+            m.chunk = auto_chunk(mc->paths_per_node, p->n_mc);
+            m.chunks_per_node = (uint32_t)((mc->paths_per_node + m.chunk - 1) / m.chunk);
+        }
+    }
+    const uint64_t items = (uint64_t)m.n_nodes * m.chunks_per_node;
     if ((rc = ensure_mc_buffers(p, items, stream))) return rc;
-    m.nodes = p->d_nodes;
+    m.nodes = few ? p->d_mc_nodes : p->d_nodes;
+    m.node_ids = few ? p->d_mc_ids : nullptr;
     m.edges = p->d_edges;
     m.sums = sums_dev ? sums_dev : p->d_sums;
-    m.mean = mean_dev ? mean_dev : p->d_mean;
-    m.stderr_ = stderr_dev ? stderr_dev : p->d_stderr;
+    // interpolation reads the plan's own output buffers
+    m.mean = few ? p->d_mean : (mean_dev ? mean_dev : p->d_mean);
+    m.stderr_ = few ? p->d_stderr : (stderr_dev ? stderr_dev : p->d_stderr);
     m.stats = p->d_stats;
+    if (few && m.sums)
+        SDD_CUDA(cudaMemsetAsync(m.sums, 0, (size_t)p->n_nodes * sizeof(sdd_node_sums), stream));
     for (int r = 0; r < 10; ++r) {
         a.rk[2 * r] = m.key0 + (uint32_t)r * 0x9E3779B9u;
         a.rk[2 * r + 1] = m.key1 + (uint32_t)r * 0xBB67AE85u;
@@ -337,11 +349,19 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     a.meshes = nullptr;
     a.n_meshes = 1;
     a.total_items = items;
-    a.total_nodes = (uint64_t)p->n_nodes;
+    a.total_nodes = (uint64_t)m.n_nodes;
     a.queue = p->d_queue;
     a.slots = p->d_slots;
     SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
     if ((rc = launch_mc(a, mc->precision, mesh_fam_class(m.family, m.nb), stream))) return rc;
+    if (few) {
+        if ((rc = launch_interp(p->d_interp, (int64_t)p->h_interp.size(), stream))) return rc;
+        const size_t bytes = (size_t)p->n_nodes * 2 * sizeof(double);
+        if (mean_dev && mean_dev != p->d_mean)
+            SDD_CUDA(cudaMemcpyAsync(mean_dev, p->d_mean, bytes, cudaMemcpyDeviceToDevice, stream));
+        if (stderr_dev && stderr_dev != p->d_stderr)
+            SDD_CUDA(cudaMemcpyAsync(stderr_dev, p->d_stderr, bytes, cudaMemcpyDeviceToDevice, stream));
+    }
     if (!p->mc_done) SDD_CUDA(cudaEventCreateWithFlags(&p->mc_done, cudaEventDisableTiming));
     SDD_CUDA(cudaEventRecord(p->mc_done, stream));
     p->last_paths = mc->paths_per_node;
@@ -369,7 +389,7 @@ int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
     McStatsDev s;
     SDD_CUDA(cudaMemcpyAsync(&s, p->d_stats, sizeof(s), cudaMemcpyDeviceToHost, stream));
     SDD_CUDA(cudaStreamSynchronize(stream));
-    return stats_from_dev(s, p->last_paths * (uint64_t)p->n_nodes, out);
+    return stats_from_dev(s, p->last_paths * (uint64_t)p->n_mc, out);
 }
 
 int validate_solve(const sdd_solve_params* sp)
@@ -446,6 +466,118 @@ int read_solve_stats(sdd_plan* p, sdd_solve_stats* out, cudaStream_t stream)
                : fail(SDD_ERR_NOT_CONVERGED, "a subdomain did not reach the tolerance");
 }
 
+// ----------------------------------------------------- few-point interface --
+// Monte Carlo nodes of a placement (§3.6): every crossing of two interface
+// lines, plus per line either k equispaced points (positions
+// round(r (m-1)/(k+1)), r = 1..k, m = points on the line including its two
+// boundary ends) or the nodes where the first or the second centred
+// difference of the density w along the line has a local extremum.
+std::vector<uint8_t> placement_mask(const sdd_plan* p, int mode, int k)
+{
+    const int n = p->n;
+    std::vector<uint8_t> mask(p->n_nodes, mode == SDD_PLACE_ALL ? 1 : 0);
+    if (mode == SDD_PLACE_ALL) return mask;
+    std::vector<int64_t> index((size_t)n * n, -1);
+    for (int64_t q = 0; q < p->n_nodes; ++q)
+        index[(size_t)p->h_nodes[2 * q + 1] * n + p->h_nodes[2 * q]] = q;
+    std::vector<char> onx(n, 0), ony(n, 0);
+    for (int v : p->ix) onx[v] = 1;
+    for (int v : p->iy) ony[v] = 1;
+    for (int64_t q = 0; q < p->n_nodes; ++q)
+        if (onx[p->h_nodes[2 * q]] && ony[p->h_nodes[2 * q + 1]]) mask[q] = 1;
+    sdd_density w = p->dens;
+    w.coef_mode = SDD_COEF_W;
+    const double h = 1.0 / (double)(n - 1);
+    auto mark_line = [&](bool vertical, int line) {
+        const int m = n;
+        auto node_at = [&](int r) -> int64_t {
+            return vertical ? index[(size_t)r * n + line] : index[(size_t)line * n + r];
+        };
+        std::vector<int> chosen;
+        if (mode == SDD_PLACE_EQUISPACED) {
+            for (int r = 1; r <= k; ++r) chosen.push_back((int)((2LL * r * (m - 1) + (k + 1)) / (2LL * (k + 1))));
+        } else {
+            std::vector<double> rho(m), d1(m, 0.0), d2(m, 0.0);
+            for (int r = 0; r < m; ++r) {
+                const double a = (double)line * h, b = (double)r * h;
+                rho[r] = vertical ? host_coef(w, a, b) : host_coef(w, b, a);
+            }
+            for (int r = 1; r < m - 1; ++r) {
+                d1[r] = (rho[r + 1] - rho[r - 1]) / (2 * h);
+                d2[r] = (rho[r + 1] - 2 * rho[r] + rho[r - 1]) / (h * h);
+            }
+            for (const std::vector<double>* dv : {&d1, &d2}) {
+                const std::vector<double>& d = *dv;
+                for (int r = 2; r < m - 2; ++r)
+                    if ((d[r] > d[r - 1] && d[r] >= d[r + 1]) || (d[r] < d[r - 1] && d[r] <= d[r + 1]))
+                        chosen.push_back(r);
+            }
+        }
+        for (int r : chosen)
+            if (r >= 1 && r <= m - 2) {
+                const int64_t q = node_at(r);
+                if (q >= 0) mask[q] = 1;
+            }
+    };
+    for (int v : p->ix) mark_line(true, v);
+    for (int v : p->iy) mark_line(false, v);
+    return mask;
+}
+
+// Interpolation entries of the non-Monte-Carlo interface nodes: along each
+// line, between the nearest Monte Carlo nodes (or the line's boundary ends,
+// boundary map); vertical lines first.
+std::vector<InterpEntry> interp_entries(const sdd_plan* p, const std::vector<uint8_t>& mask)
+{
+    const int n = p->n;
+    std::vector<int64_t> index((size_t)n * n, -1);
+    for (int64_t q = 0; q < p->n_nodes; ++q)
+        index[(size_t)p->h_nodes[2 * q + 1] * n + p->h_nodes[2 * q]] = q;
+    auto bvalue = [&](int i, int j, int c) -> double {
+        // boundary grid: rows j = 0, n-1 from the bottom/top tables, else columns
+        const auto E = [&](int comp, int edge, int kk) { return p->h_edges[((size_t)comp * 4 + edge) * n + kk]; };
+        if (j == 0) return E(c, 0, i);
+        if (j == n - 1) return E(c, 1, i);
+        if (i == 0) return E(c, 2, j);
+        return E(c, 3, j);
+    };
+    std::vector<InterpEntry> out;
+    auto do_line = [&](bool vertical, int line) {
+        auto ij = [&](int r, int& i, int& j) { if (vertical) { i = line; j = r; } else { i = r; j = line; } };
+        std::vector<int> known;
+        for (int r = 0; r < n; ++r) {
+            int i, j;
+            ij(r, i, j);
+            if (r == 0 || r == n - 1) { known.push_back(r); continue; }
+            const int64_t q = index[(size_t)j * n + i];
+            if (q >= 0 && mask[q]) known.push_back(r);
+        }
+        for (size_t kk = 0; kk + 1 < known.size(); ++kk) {
+            const int ra = known[kk], rb = known[kk + 1];
+            for (int r = ra + 1; r < rb; ++r) {
+                int i, j, ia, ja, ib, jb;
+                ij(r, i, j);
+                ij(ra, ia, ja);
+                ij(rb, ib, jb);
+                InterpEntry e;
+                memset(&e, 0, sizeof(e));
+                e.q = index[(size_t)j * n + i];
+                e.w = (double)(r - ra) / (double)(rb - ra);
+                e.a = (ra == 0 || ra == n - 1) ? -1 : index[(size_t)ja * n + ia];
+                e.b = (rb == 0 || rb == n - 1) ? -1 : index[(size_t)jb * n + ib];
+                for (int c = 0; c < 2; ++c) {
+                    e.ca[c] = e.a < 0 ? bvalue(ia, ja, c) : 0.0;
+                    e.cb[c] = e.b < 0 ? bvalue(ib, jb, c) : 0.0;
+                }
+                out.push_back(e);
+            }
+        }
+    };
+    for (int v : p->ix) do_line(true, v);
+    for (int v : p->iy) do_line(false, v);
+    return out;
+}
+
 // ------------------------------------------------------------------ batch --
 // Many plans generated together: one path-kernel launch per (precision,
 // density class) group over all their interface nodes, one reduction per
@@ -480,6 +612,8 @@ struct sdd_batch {
     sdd::SolveMeshDev* d_smesh = nullptr;
     sdd::SubDev* d_subs = nullptr;
     sdd::SubStat* d_substats = nullptr;
+    sdd::InterpEntry* d_interp = nullptr;       // few-point interfaces of the plans
+    int64_t n_interp = 0;
     std::vector<int> sub_begin;                 // plan -> first subdomain
     int n_subs = 0;
     int solver_mask = 0;                        // solvers used by the batch's plans
@@ -509,6 +643,7 @@ void batch_free(sdd_batch* b)
     dev_free(b->d_smesh, fs);
     dev_free(b->d_subs, fs);
     dev_free(b->d_substats, fs);
+    dev_free(b->d_interp, fs);
     delete b;
 }
 
@@ -523,6 +658,8 @@ int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
             int rc = launch_mc_sized(g.args, g.precision, g.fc, g.blocks, stream);
             if (rc) return rc;
         }
+        int rc = launch_interp(b->d_interp, b->n_interp, stream);
+        if (rc) return rc;
     }
     if (phases & 2) {
         for (sdd_plan* p : b->plans) {                 // first solve: edge coefficients
@@ -598,6 +735,8 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
                 p->h_nodes.push_back(j);
             }
     p->n_nodes = (int64_t)p->h_nodes.size() / 2;
+    p->n_mc = p->n_nodes;
+    p->h_mask.assign(p->n_nodes, 1);
 
     // subdomain boxes
     std::vector<int> X{0}, Y{0};
@@ -756,7 +895,7 @@ int sdd_plan_last_mc_stats(sdd_plan* p, sdd_mc_stats* stats)
     SDD_CUDA(cudaEventSynchronize(p->mc_done));
     McStatsDev s;
     SDD_CUDA(cudaMemcpy(&s, p->d_stats, sizeof(s), cudaMemcpyDeviceToHost));
-    return stats_from_dev(s, p->last_paths * (uint64_t)p->n_nodes, stats);
+    return stats_from_dev(s, p->last_paths * (uint64_t)p->n_mc, stats);
 }
 
 int sdd_subdomain_solve(sdd_plan* p, const double* iface, const sdd_solve_params* sp, double* mesh,
@@ -847,6 +986,10 @@ void sdd_plan_destroy(sdd_plan* p)
     dev_free(p->d_work, fs);
     dev_free(p->d_subs, fs);
     dev_free(p->d_substats, fs);
+    dev_free(p->d_mc_nodes, fs);
+    dev_free(p->d_mc_ids, fs);
+    dev_free(p->d_interp, fs);
+    dev_free(p->d_quality, fs);
     if (p->mc_done) cudaEventDestroy(p->mc_done);
     delete p;
 }
@@ -857,6 +1000,121 @@ int sdd_kernel_launches(uint64_t* count)
 {
     if (!count) return fail(SDD_ERR_INVALID_ARG, "count is NULL");
     *count = g_launches.load(std::memory_order_relaxed);
+    return SDD_OK;
+}
+
+int sdd_plan_set_placement(sdd_plan* p, int mode, int k)
+{
+    clear_error();
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "plan is NULL");
+    if (mode != SDD_PLACE_ALL && mode != SDD_PLACE_EQUISPACED && mode != SDD_PLACE_EXTREMA)
+        return fail(SDD_ERR_INVALID_ARG, "unknown placement mode");
+    if (mode == SDD_PLACE_EQUISPACED && (k < 1 || k > p->n - 2))
+        return fail(SDD_ERR_INVALID_ARG, "EQUISPACED needs 1 <= k <= n-2");
+    int rc = check_device(p);
+    if (rc) return rc;
+    std::vector<uint8_t> mask = placement_mask(p, mode, k);
+    std::vector<int32_t> sub;
+    std::vector<uint32_t> ids;
+    for (int64_t q = 0; q < p->n_nodes; ++q)
+        if (mask[q]) {
+            sub.push_back(p->h_nodes[2 * q]);
+            sub.push_back(p->h_nodes[2 * q + 1]);
+            ids.push_back((uint32_t)q);
+        }
+    const cudaStream_t ss = setup_stream();
+    // the old placement's buffers may still be read by queued work
+    const cudaStream_t fs = p->last_stream ? p->last_stream : ss;
+    dev_free(p->d_mc_nodes, fs);
+    dev_free(p->d_mc_ids, fs);
+    dev_free(p->d_interp, fs);
+    p->h_interp.clear();
+    p->place_mode = mode;
+    p->h_mask = mask;
+    p->n_mc = (int64_t)ids.size();
+    if (p->n_mc == p->n_nodes) return SDD_OK;           // every node: the plain path
+    if ((rc = ensure_mc_buffers(p, 0, ss))) return rc;
+    std::vector<InterpEntry> ent = interp_entries(p, mask);
+    for (InterpEntry& e : ent) {
+        e.mean = p->d_mean;
+        e.se = p->d_stderr;
+    }
+    AllocOn on(ss);
+    if ((rc = dev_alloc(&p->d_mc_nodes, std::max<size_t>(ids.size(), 1))) ||
+        (rc = dev_alloc(&p->d_mc_ids, std::max<size_t>(ids.size(), 1))) ||
+        (rc = dev_alloc(&p->d_interp, std::max<size_t>(ent.size(), 1))))
+        return rc;
+    if (!ids.empty()) {
+        SDD_CUDA(cudaMemcpyAsync(p->d_mc_nodes, sub.data(), sub.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, ss));
+        SDD_CUDA(cudaMemcpyAsync(p->d_mc_ids, ids.data(), ids.size() * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, ss));
+    }
+    if (!ent.empty())
+        SDD_CUDA(cudaMemcpyAsync(p->d_interp, ent.data(), ent.size() * sizeof(InterpEntry),
+                                 cudaMemcpyHostToDevice, ss));
+    SDD_CUDA(cudaStreamSynchronize(ss));
+    p->h_interp = std::move(ent);
+    return SDD_OK;
+}
+
+int sdd_plan_placement(const sdd_plan* p, uint8_t* mask, int64_t* n_mc)
+{
+    clear_error();
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "plan is NULL");
+    if (mask) std::copy(p->h_mask.begin(), p->h_mask.end(), mask);
+    if (n_mc) *n_mc = p->n_mc;
+    return SDD_OK;
+}
+
+int sdd_mesh_quality(sdd_plan* p, const double* mesh, const double* ref, sdd_quality* out,
+                     void* stream_)
+{
+    clear_error();
+    if (!p || !mesh || !out) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_device(p);
+    if (rc) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    const size_t bytes = (size_t)p->n * p->n * 2 * sizeof(double);
+    double* tmp = nullptr;                       // device copies of host meshes
+    const double* dm = mesh;
+    const double* dr = ref;
+    {
+        AllocOn on(stream);
+        const bool hm = !is_device_ptr(mesh), hr = ref && !is_device_ptr(ref);
+        if (hm || hr) {
+            if ((rc = dev_alloc(&tmp, (hm ? 2 : 0) * (size_t)p->n * p->n + (hr ? 2 : 0) * (size_t)p->n * p->n)))
+                return rc;
+            double* q = tmp;
+            if (hm) {
+                SDD_CUDA(cudaMemcpyAsync(q, mesh, bytes, cudaMemcpyHostToDevice, stream));
+                dm = q;
+                q += 2 * (size_t)p->n * p->n;
+            }
+            if (hr) {
+                SDD_CUDA(cudaMemcpyAsync(q, ref, bytes, cudaMemcpyHostToDevice, stream));
+                dr = q;
+            }
+        }
+        if (!p->d_quality && (rc = dev_alloc(&p->d_quality, 1))) return rc;
+    }
+    rc = launch_quality(p->n, p->dens.family, p->dens.params, dm, dr, p->d_quality, stream);
+    if (rc) return rc;
+    QualityDev q;
+    SDD_CUDA(cudaMemcpyAsync(&q, p->d_quality, sizeof(q), cudaMemcpyDeviceToHost, stream));
+    if (tmp) dev_free(tmp, stream);
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    const double cells = (double)(p->n - 1) * (p->n - 1);
+    auto dbl = [](unsigned long long b) { double d; memcpy(&d, &b, sizeof(d)); return d; };
+    out->q_max = dbl(q.q_max_bits);
+    out->folds = (int64_t)q.folds;
+    out->q_mean = q.q_sum / std::max(cells - (double)q.folds, 1.0);
+    out->ref_q_max = ref ? dbl(q.q_ref_max_bits) : 0.0;
+    out->ref_folds = ref ? (int64_t)q.ref_folds : 0;
+    out->ref_q_mean = ref ? q.q_ref_sum / std::max(cells - (double)q.ref_folds, 1.0) : 0.0;
+    out->r_max = ref && out->q_max > 0 ? out->ref_q_max / out->q_max : 0.0;
+    out->r_mean = ref && out->q_mean > 0 ? out->ref_q_mean / out->q_mean : 0.0;
+    out->l_inf = ref ? dbl(q.l_inf_bits) : 0.0;
     return SDD_OK;
 }
 
@@ -920,9 +1178,16 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
             const int i = order[q];
             MeshDev& m = recs[q];
             mesh_record(plans[i], &mc[i], m);
+            if (plans[i]->n_mc < plans[i]->n_nodes) {          // few-point interface
+                m.n_nodes = plans[i]->n_mc;
+                if (!mc[i].chunk) {
+                    m.chunk = auto_chunk(mc[i].paths_per_node, plans[i]->n_mc);
+                    m.chunks_per_node = (uint32_t)((mc[i].paths_per_node + m.chunk - 1) / m.chunk);
+                }
+            }
             m.item_begin = it;
             offs.push_back(it);
-            it += (uint64_t)plans[i]->n_nodes * m.chunks_per_node;
+            it += (uint64_t)m.n_nodes * m.chunks_per_node;
             b->plan_slot[i] = q;
         }
         offs.push_back(it);
@@ -932,7 +1197,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         for (int q = k; q < e; ++q) {
             recs[q].node_begin = nd;
             offs.push_back(nd);
-            nd += (uint64_t)plans[order[q]]->n_nodes;
+            nd += (uint64_t)recs[q].n_nodes;
         }
         offs.push_back(nd);
         g.nodes = nd;
@@ -995,12 +1260,32 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         return rc;
     }
     // outputs of each record: the plan's own buffers; stats per plan
+    std::vector<InterpEntry> interp;
     for (int i = 0; i < n_plans; ++i) {
         MeshDev& m = recs[b->plan_slot[i]];
         m.sums = plans[i]->d_sums;
         m.mean = plans[i]->d_mean;
         m.stderr_ = plans[i]->d_stderr;
         m.stats = b->d_stats + i;
+        if (plans[i]->n_mc < plans[i]->n_nodes) {
+            m.nodes = plans[i]->d_mc_nodes;
+            m.node_ids = plans[i]->d_mc_ids;
+            interp.insert(interp.end(), plans[i]->h_interp.begin(), plans[i]->h_interp.end());
+        }
+    }
+    b->n_interp = (int64_t)interp.size();
+    if (!interp.empty()) {
+        if ((rc = dev_alloc(&b->d_interp, interp.size()))) {
+            batch_free(b);
+            return rc;
+        }
+        cudaError_t ie = cudaMemcpyAsync(b->d_interp, interp.data(), interp.size() * sizeof(InterpEntry),
+                                         cudaMemcpyHostToDevice, ss);
+        if (ie != cudaSuccess) {
+            rc = cuda_status(ie, "cudaMemcpyAsync(batch interpolation)");
+            batch_free(b);
+            return rc;
+        }
     }
     const auto h2d = cudaMemcpyHostToDevice;
     cudaError_t ce = cudaMemcpyAsync(b->d_meshes, recs.data(), recs.size() * sizeof(MeshDev), h2d, ss);
@@ -1128,7 +1413,7 @@ int sdd_batch_plan_stats(sdd_batch* b, int index, sdd_mc_stats* mc, sdd_solve_st
     if (mc) {
         McStatsDev s;
         SDD_CUDA(cudaMemcpy(&s, b->d_stats + index, sizeof(s), cudaMemcpyDeviceToHost));
-        if ((rc = stats_from_dev(s, b->plan_paths[index] * (uint64_t)p->n_nodes, mc))) return rc;
+        if ((rc = stats_from_dev(s, b->plan_paths[index] * (uint64_t)p->n_mc, mc))) return rc;
     }
     if (solve) {
         const int nsub = (int)p->h_subs.size();

@@ -56,7 +56,9 @@ struct MeshDev {
     double sqrt2dt;
     double tie_delta;
     double sgn;             // +1: c = w, -1: c = 1/w
-    const int2* nodes;      // [n_nodes] (i, j)
+    const int2* nodes;      // [n_nodes] (i, j) of the nodes the Monte Carlo runs on
+    const uint32_t* node_ids;  // their index in the plan's interface list (Philox
+                               // counter word, output row); NULL: the position itself
     const double* edges;    // [2][4][n]
     sdd_node_sums* sums;    // [n_nodes] out
     double* mean;           // [n_nodes][2] out (may be null)
@@ -101,6 +103,27 @@ struct McArgs {
 // kFamAny selects the kernel that handles every class.
 int mesh_fam_class(int family, int nb);
 constexpr int kFamAny = 6;
+
+// Interpolated interface node of a few-point interface (§3.6): value =
+// (1 - w) A + w B per component, A / B the mean (and std-err) of interface
+// node a / b, or the boundary-map constant ca / cb when a / b < 0.
+struct InterpEntry {
+    double* mean;           // [n_nodes][2] of the plan
+    double* se;             // may be null
+    int64_t q, a, b;
+    double w;
+    double ca[2], cb[2];
+};
+int launch_interp(const InterpEntry* d_entries, int64_t count, cudaStream_t stream);
+
+// Mesh quality: cells' Q(K) (max, sum, folds) of `u` and of `ref`, l_inf of w.
+struct QualityDev {
+    unsigned long long q_max_bits, q_ref_max_bits;
+    double q_sum, q_ref_sum;
+    unsigned long long folds, ref_folds, l_inf_bits;
+};
+int launch_quality(int n, int family, const double* params, const double* u, const double* ref,
+                   QualityDev* d_out, cudaStream_t stream);
 
 // Launches the path kernel (for density class `fc`) and the per-node
 // reduction.
@@ -218,6 +241,18 @@ struct sdd_plan {
     sdd::SubDev* d_subs = nullptr;
     sdd::SubStat* d_substats = nullptr;
     bool coefs_ready = false;
+
+    // few-point interface: Monte Carlo on a subset, interpolation for the rest
+    int place_mode = 0;
+    std::vector<uint8_t> h_mask;           // [n_nodes] 1 = Monte Carlo node
+    int64_t n_mc = 0;                      // nodes the Monte Carlo runs on
+    int2* d_mc_nodes = nullptr;            // [n_mc]
+    uint32_t* d_mc_ids = nullptr;          // [n_mc] index in the interface list
+    std::vector<sdd::InterpEntry> h_interp;   // pointers filled per call
+    sdd::InterpEntry* d_interp = nullptr;
+    double* d_interp_mean = nullptr;       // outputs the device entries point at
+    double* d_interp_se = nullptr;
+    sdd::QualityDev* d_quality = nullptr;
 
     cudaStream_t last_stream = nullptr;
 };

@@ -17,6 +17,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sdd_internal.h"
 
 namespace sdd {
@@ -203,7 +205,6 @@ struct Box {
         nx = i1 - i0 - 1;
         ny = j1 - j0 - 1;
     }
-    __device__ bool interior(int i, int j) const { return i > i0 && i < i1 && j > j0 && j < j1; }
 };
 
 // FP64 residual  r_ij = sum_nbr c (u_nbr - u_ij)  (= (b - A u)_ij) at node (i,j).
@@ -490,7 +491,96 @@ k_solve(SolveArgs a)
     if (threadIdx.x == 0) a.stats[sd.slot] = st;
 }
 
+// Mesh quality (§3.1, §3.3): per cell the Jacobian of (s,t) -> u from the
+// mean of the cell's two edge differences per direction, Q = 1/2 |J|_F^2 /
+// det J (folded when det J <= 0); per node |w(u) - w(ref)|.  Block
+// reductions, then atomics (max of non-negative bit patterns, sums).
+__device__ __forceinline__ bool cell_q(const double2* __restrict__ u, int n, int i, int j, double& q)
+{
+    const double h = 1.0 / (double)(n - 1);
+    const double2 a00 = u[(int64_t)j * n + i], a10 = u[(int64_t)j * n + i + 1];
+    const double2 a01 = u[(int64_t)(j + 1) * n + i], a11 = u[(int64_t)(j + 1) * n + i + 1];
+    const double xs = ((a10.x - a00.x) + (a11.x - a01.x)) / (2 * h);
+    const double ys = ((a10.y - a00.y) + (a11.y - a01.y)) / (2 * h);
+    const double xt = ((a01.x - a00.x) + (a11.x - a10.x)) / (2 * h);
+    const double yt = ((a01.y - a00.y) + (a11.y - a10.y)) / (2 * h);
+    const double det = xs * yt - xt * ys;
+    if (!(det > 0.0)) return false;
+    q = 0.5 * (xs * xs + xt * xt + ys * ys + yt * yt) / det;
+    return true;
+}
+
+struct QualityArgs {
+    int n, family;
+    double p[SDD_MAX_PARAMS];
+};
+
+__global__ void __launch_bounds__(256) k_quality(QualityArgs a, const double2* __restrict__ u,
+                                                 const double2* __restrict__ ref,
+                                                 QualityDev* __restrict__ out)
+{
+    __shared__ double scratch[128];
+    const int n = a.n;
+    const int64_t cells = (int64_t)(n - 1) * (n - 1);
+    const int64_t nodes = (int64_t)n * n;
+    double qmax[2] = {0.0, 0.0}, qsum[2] = {0.0, 0.0}, linf = 0.0;
+    unsigned long long folds[2] = {0ull, 0ull};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nodes; g += stride) {
+        const int i = (int)(g % n), j = (int)(g / n);
+        if (g < nodes && i < n - 1 && j < n - 1) {
+            double q;
+            if (cell_q(u, n, i, j, q)) { qmax[0] = fmax(qmax[0], q); qsum[0] += q; } else ++folds[0];
+            if (ref) {
+                if (cell_q(ref, n, i, j, q)) { qmax[1] = fmax(qmax[1], q); qsum[1] += q; } else ++folds[1];
+            }
+        }
+        if (ref) {
+            const double2 x = u[g], y = ref[g];
+            linf = fmax(linf, fabs(coef64(a.family, SDD_COEF_W, a.p, x.x, x.y) -
+                                   coef64(a.family, SDD_COEF_W, a.p, y.x, y.y)));
+        }
+    }
+    (void)cells;
+    double v[4] = {qsum[0], qsum[1], (double)folds[0], (double)folds[1]};
+    block_sum<double, 4>(v, scratch);
+    // maxima: warp then block by shuffles and shared memory
+    double m[3] = {qmax[0], qmax[1], linf};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m[q] = fmax(m[q], __shfl_xor_sync(0xffffffffu, m[q], off));
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out->q_max_bits, (unsigned long long)__double_as_longlong(m[0]));
+        atomicMax(&out->q_ref_max_bits, (unsigned long long)__double_as_longlong(m[1]));
+        atomicMax(&out->l_inf_bits, (unsigned long long)__double_as_longlong(m[2]));
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&out->q_sum, v[0]);
+        atomicAdd(&out->q_ref_sum, v[1]);
+        atomicAdd(&out->folds, (unsigned long long)v[2]);
+        atomicAdd(&out->ref_folds, (unsigned long long)v[3]);
+    }
+}
+
 }  // namespace
+
+int launch_quality(int n, int family, const double* params, const double* u, const double* ref,
+                   QualityDev* d_out, cudaStream_t stream)
+{
+    QualityArgs a;
+    a.n = n;
+    a.family = family;
+    for (int q = 0; q < SDD_MAX_PARAMS; ++q) a.p[q] = params[q];
+    SDD_CUDA(cudaMemsetAsync(d_out, 0, sizeof(QualityDev), stream));
+    const int64_t nodes = (int64_t)n * n;
+    const unsigned blocks = (unsigned)std::min<int64_t>((nodes + 255) / 256, 4096);
+    k_quality<<<blocks, 256, 0, stream>>>(a, reinterpret_cast<const double2*>(u),
+                                          reinterpret_cast<const double2*>(ref), d_out);
+    SDD_CUDA(cudaGetLastError());
+    count_launch();
+    return SDD_OK;
+}
 
 int launch_edge_coefs(int n, int family, int coef_mode, const double* params, double* cx,
                       double* cy, float* cxf, float* cyf, cudaStream_t stream)

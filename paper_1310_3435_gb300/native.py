@@ -34,6 +34,7 @@ SDD_BMAP_IDENTITY, SDD_BMAP_PAPER_1D, SDD_BMAP_TABLE = 0, 1, 2
 SDD_FP64, SDD_FP32_STEP = 0, 1
 SDD_SOLVER_SOR, SDD_SOLVER_CG_FP32_REFINE = 0, 1
 SDD_EXIT_END_OF_STEP, SDD_EXIT_BRIDGE = 0, 1
+SDD_PLACE_ALL, SDD_PLACE_EQUISPACED, SDD_PLACE_EXTREMA = 0, 1, 2
 
 
 class SddError(RuntimeError):
@@ -85,6 +86,14 @@ class sdd_solve_params(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("omega", ctypes.c_double),
                 ("block_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sdd_quality(ctypes.Structure):
+    _fields_ = [("q_max", ctypes.c_double), ("q_mean", ctypes.c_double),
+                ("folds", ctypes.c_int64), ("ref_q_max", ctypes.c_double),
+                ("ref_q_mean", ctypes.c_double), ("ref_folds", ctypes.c_int64),
+                ("r_max", ctypes.c_double), ("r_mean", ctypes.c_double),
+                ("l_inf", ctypes.c_double)]
 
 
 class sdd_solve_stats(ctypes.Structure):
@@ -150,11 +159,15 @@ def load(build_if_missing: bool = True):
     L.sdd_batch_destroy.restype = None
     L.sdd_interface_mc_static.argtypes = [ctypes.c_int, vp, ctypes.c_int64, vp, P(sdd_density),
                                           P(sdd_mc_params), vp, vp, vp]
+    L.sdd_plan_set_placement.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.sdd_plan_placement.argtypes = [vp, vp, P(ctypes.c_int64)]
+    L.sdd_mesh_quality.argtypes = [vp, vp, vp, P(sdd_quality), vp]
     for name in ("sdd_mesh_plan", "sdd_plan_num_nodes", "sdd_plan_nodes", "sdd_plan_edges",
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
                  "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
                  "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
-                 "sdd_batch_plan_stats", "sdd_interface_mc_static"):
+                 "sdd_batch_plan_stats", "sdd_interface_mc_static", "sdd_plan_set_placement",
+                 "sdd_plan_placement", "sdd_mesh_quality"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -363,6 +376,25 @@ def sdd_interface_mc_static(n: int, nodes, edges, density: sdd_density, mc: sdd_
                                           ctypes.byref(density), ctypes.byref(mc), _ptr(mean),
                                           _ptr(stderr), _stream(stream)),
            "sdd_interface_mc_static")
+
+
+def sdd_plan_set_placement(plan, mode: int, k: int = 7) -> None:
+    _check(load().sdd_plan_set_placement(plan, int(mode), int(k)), "sdd_plan_set_placement")
+
+
+def sdd_plan_placement(plan):
+    """(mask [n_nodes] bool, number of Monte Carlo nodes)."""
+    m = np.zeros(sdd_plan_num_nodes(plan), dtype=np.uint8)
+    c = ctypes.c_int64()
+    _check(load().sdd_plan_placement(plan, _ptr(m), ctypes.byref(c)), "sdd_plan_placement")
+    return m.astype(bool), int(c.value)
+
+
+def sdd_mesh_quality(plan, mesh, ref=None, stream=None) -> dict:
+    q = sdd_quality()
+    _check(load().sdd_mesh_quality(plan, _ptr(mesh), _ptr(ref), ctypes.byref(q), _stream(stream)),
+           "sdd_mesh_quality")
+    return {name: getattr(q, name) for name, _ in sdd_quality._fields_}
 
 
 def sdd_plan_destroy(plan) -> None:
