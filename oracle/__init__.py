@@ -74,15 +74,18 @@ def lib():
         L.oracle_path.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_uint32, ctypes.c_uint32, dp, ctypes.c_int,
                                   ctypes.c_int, dp, ctypes.c_uint64, ctypes.c_double,
-                                  ctypes.c_uint64, ctypes.c_double, ctypes.c_int, dp, u64p, ip,
-                                  ip]
+                                  ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  dp, u64p, ip, ip]
         L.oracle_path.restype = None
         L.oracle_mc_node.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_uint32, dp, ctypes.c_int, ctypes.c_int, dp,
                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_double,
-                                     ctypes.c_int, dp, u64p]
+                                     ctypes.c_int, ctypes.c_int, dp, u64p]
         L.oracle_mc_node.restype = None
+        L.oracle_step_lengths.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_uint32, dp]
+        L.oracle_step_lengths.restype = None
         L.oracle_bridge_exit.argtypes = [ctypes.c_double] * 5 + [ctypes.c_uint64, ctypes.c_uint32,
                                                                  ctypes.c_uint32, ctypes.c_uint32,
                                                                  dp, ip]
@@ -226,12 +229,13 @@ def default_threads() -> int:
 def mc_nodes(n: int, nodes, edges: np.ndarray, family: int, coef_mode: int, params,
              seed: int, paths: int, dt: float, max_steps: int, tie_delta: float = 0.0,
              node_ids=None, threads: int | None = None, path_begin: int = 0,
-             exit_test: int = 0) -> dict:
+             exit_test: int = 0, stepper: int = 0) -> dict:
     """Per-node Monte Carlo sums (§2.2) for nodes [(i, j), ...].
 
     Node m uses counter word node_ids[m] (default: m) and paths
     [path_begin, path_begin + paths).  exit_test: 0 end-of-step test only,
-    1 also the Brownian-bridge test (§2.2).  Returns arrays
+    1 also the Brownian-bridge test (§2.2).  stepper: 0 constant step dt,
+    1 exponential time stepping with mean step dt (§2.2).  Returns arrays
       S_all, Q_all, S_nt, Q_nt : [n_nodes, 2]  sums of d = F - X0 and d^2 over
                                  all paths / paths not flagged as ties
       paths, ties, non_exits, steps : [n_nodes] uint64
@@ -251,7 +255,7 @@ def mc_nodes(n: int, nodes, edges: np.ndarray, family: int, coef_mode: int, para
         crow = counts[k]
         L.oracle_mc_node(n, i, j, int(ids[k]) & 0xFFFFFFFF, _dp(E), family, coef_mode,
                          _dp(p), seed, path_begin, path_begin + paths, dt, max_steps,
-                         tie_delta, exit_test,
+                         tie_delta, exit_test, stepper,
                          srow.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          crow.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
 
@@ -283,7 +287,7 @@ def mc_estimate(nodes, n: int, S: np.ndarray, Q: np.ndarray, N) -> tuple:
 
 def path(n: int, s0: float, t0: float, node: int, path_index: int, edges: np.ndarray,
          family: int, coef_mode: int, params, seed: int, dt: float, max_steps: int,
-         tie_delta: float = 0.0, exit_test: int = 0) -> dict:
+         tie_delta: float = 0.0, exit_test: int = 0, stepper: int = 0) -> dict:
     """One path from (s0, t0): score, step count, tie and cap flags."""
     E = np.ascontiguousarray(edges, dtype=np.float64)
     p = _params(params)
@@ -292,9 +296,18 @@ def path(n: int, s0: float, t0: float, node: int, path_index: int, edges: np.nda
     tie = ctypes.c_int()
     cap = ctypes.c_int()
     lib().oracle_path(n, s0, t0, node, path_index, _dp(E), family, coef_mode, _dp(p),
-                      seed, dt, max_steps, tie_delta, exit_test, _dp(F), ctypes.byref(st),
+                      seed, dt, max_steps, tie_delta, exit_test, stepper, _dp(F),
+                      ctypes.byref(st),
                       ctypes.byref(tie), ctypes.byref(cap))
     return {"F": F, "steps": int(st.value), "tie": bool(tie.value), "capped": bool(cap.value)}
+
+
+def step_lengths(seed: int, node: int, path: int, step_pair: int) -> np.ndarray:
+    """Unit-mean exponentials of the lengths of steps 2 step_pair and
+    2 step_pair + 1 under exponential time stepping (§2.2)."""
+    E = np.zeros(2, dtype=np.float64)
+    lib().oracle_step_lengths(seed, node, path, step_pair, _dp(E))
+    return E
 
 
 def exit_point(xs: float, xt: float, ys: float, yt: float):

@@ -31,6 +31,16 @@
  *   step k   : R = sqrt(-2 ln U0), z = (R cos 2 pi U1, R sin 2 pi U1)
  *   step k+1 : R = sqrt(-2 ln U2), z = (R cos 2 pi U3, R sin 2 pi U3)
  *
+ * Exponential time stepping (§2.2, after Jansons and Lythe): step k has the
+ * random length h_k = dt E_k, E_k = -ln U a unit-mean exponential, so the
+ * steps have the density lambda exp(-lambda h) with lambda = 1/dt.  The two
+ * lengths of steps k and k+1 (k even) come from words 0 and 1 of
+ * Philox(counter = (k/2, path, node, 2)).  Given h_k the update is the
+ * Euler-Maruyama one with step h_k, and the boundary test is the exact
+ * crossing probability of the step's Brownian bridge over the time h_k (the
+ * Brownian-bridge test below with dt replaced by h_k), which is how the
+ * exponential steps take their boundary test.
+ *
  * Build: plain C99, -O2 -ffp-contract=off, no fast-math (oracle/build.py).
  */
 #include <math.h>
@@ -88,6 +98,20 @@ void oracle_normals(uint64_t seed, uint32_t node, uint32_t path, uint32_t step_p
     z[1] = ra * sin(2.0 * M_PI * u[1]);
     z[2] = rb * cos(2.0 * M_PI * u[3]);
     z[3] = rb * sin(2.0 * M_PI * u[3]);
+}
+
+/* Unit-mean exponentials E_k, E_k+1 of the step lengths of steps k and k+1
+ * (k even) under exponential time stepping: E = -ln U, U = (r + 1/2) 2^-32
+ * from words 0 and 1 of Philox(counter = (k/2, path, node, 2)). */
+void oracle_step_lengths(uint64_t seed, uint32_t node, uint32_t path, uint32_t step_pair,
+                         double E[2])
+{
+    uint32_t ctr[4] = {step_pair, path, node, 2u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    oracle_philox4x32_10(ctr, key, r);
+    for (int m = 0; m < 2; ++m)
+        E[m] = -log(((double)r[m] + 0.5) * 0x1p-32);
 }
 
 /* --------------------------------------------------------------- density -- */
@@ -284,27 +308,34 @@ int oracle_bridge_exit(double xs, double xt, double ys, double yt, double dt, ui
 /* Runs path `path` from (s0,t0).  Returns the score F = (f, g) at the exit
  * point; *steps = Euler-Maruyama updates performed; *tie = 1 if any post-step
  * coordinate came within tie_delta of 0 or 1 (an exit decision that rounding
- * could flip); *capped = 1 if max_steps was reached without an exit. */
+ * could flip); *capped = 1 if max_steps was reached without an exit.
+ * stepper 0: constant step dt; 1: exponential time stepping with mean step
+ * dt (lambda = 1/dt). */
 void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
                  const double* edges, int family, int coef_mode, const double* p,
                  uint64_t seed, double dt, uint64_t max_steps, double tie_delta, int exit_test,
-                 double F[2], uint64_t* steps, int* tie, int* capped)
+                 int stepper, double F[2], uint64_t* steps, int* tie, int* capped)
 {
     double xs = s0, xt = t0;
-    double sq = sqrt(2.0 * dt);
     double z[4];
+    double E[2] = {1.0, 1.0};
     int flag = 0;
     uint64_t k = 0;
     double e[2];
     int edge = -1;
     while (k < max_steps) {
-        if ((k & 1u) == 0)
+        if ((k & 1u) == 0) {
             oracle_normals(seed, node, path, (uint32_t)(k >> 1), z);
+            if (stepper == 1)
+                oracle_step_lengths(seed, node, path, (uint32_t)(k >> 1), E);
+        }
         const double* zk = z + 2 * (int)(k & 1u);
+        double h = stepper == 1 ? dt * E[k & 1u] : dt;
+        double sq = sqrt(2.0 * h);
         double b[2];
         oracle_drift(family, coef_mode, p, xs, xt, b);
-        double ys = xs + b[0] * dt + sq * zk[0];
-        double yt = xt + b[1] * dt + sq * zk[1];
+        double ys = xs + b[0] * h + sq * zk[0];
+        double yt = xt + b[1] * h + sq * zk[1];
         k += 1;
         if (fabs(ys) < tie_delta || fabs(ys - 1.0) < tie_delta ||
             fabs(yt) < tie_delta || fabs(yt - 1.0) < tie_delta)
@@ -312,7 +343,7 @@ void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
         edge = oracle_exit_point(xs, xt, ys, yt, e);
         if (edge >= 0) break;
         if (exit_test == 1) {
-            edge = oracle_bridge_exit(xs, xt, ys, yt, dt, seed, node, path, (uint32_t)(k - 1), e,
+            edge = oracle_bridge_exit(xs, xt, ys, yt, h, seed, node, path, (uint32_t)(k - 1), e,
                                       &flag);
             if (edge >= 0) break;
         }
@@ -339,7 +370,7 @@ void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
 void oracle_mc_node(int n, int i, int j, uint32_t node, const double* edges,
                     int family, int coef_mode, const double* p, uint64_t seed,
                     uint64_t path_begin, uint64_t path_end, double dt,
-                    uint64_t max_steps, double tie_delta, int exit_test,
+                    uint64_t max_steps, double tie_delta, int exit_test, int stepper,
                     double sums[8], uint64_t counts[4])
 {
     double s0 = (double)i / (double)(n - 1);
@@ -352,7 +383,7 @@ void oracle_mc_node(int n, int i, int j, uint32_t node, const double* edges,
         uint64_t st;
         int tie, capped;
         oracle_path(n, s0, t0, node, (uint32_t)q, edges, family, coef_mode, p, seed,
-                    dt, max_steps, tie_delta, exit_test, F, &st, &tie, &capped);
+                    dt, max_steps, tie_delta, exit_test, stepper, F, &st, &tie, &capped);
         for (int c = 0; c < 2; ++c) {
             double d = F[c] - x0[c];
             sums[0 + c] += d;
