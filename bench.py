@@ -509,6 +509,48 @@ def run_precision(args):
     return 0
 
 
+def run_quality(args):
+    """Mesh-quality report on the paper's running example (eq.
+    MonitorFunctionRunningExample: rho = 1 + 15 exp(-50 (x - 3/4)^2 - 50 (y -
+    1/2)^2 - 1/2), generator coefficient 1/rho, 29 x 29 grid): the 2 x 2
+    stochastic-deterministic DD mesh against the single-domain mesh (R_max,
+    R_mean, l_inf as in §3.3, §3.5), for several N, and few-point interfaces
+    with 7 equispaced points per line against the extrema placement (§3.6).
+    Boundary map: the 1D generator on the sides (§3.2)."""
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    torch.cuda.set_device(0)
+    rho = W.bumps((15.0 * math.exp(-0.5), 0.75, 0.5, 50.0, 50.0))
+    base = dict(n=29, family=W.FAMILY_BUMPS, params=rho, coef_mode=W.COEF_INV_W,
+                bmap_mode=W.BMAP_PAPER_1D, dt=args.quality_dt, seed=0, precision=W.FP32_STEP, exit_test=W.EXIT_BRIDGE,
+                solver=W.SOLVER_SOR, tol=1e-12)
+    single = W.MeshSpec(sx=1, sy=1, paths=2, **base)
+    with N.Plan(single) as P:
+        ref = np.zeros((29, 29, 2))
+        N.sdd_subdomain_solve(P.handle, np.zeros((0, 2)), P.solve_params(), ref)
+        q_ref = N.sdd_mesh_quality(P.handle, ref)
+    rows = []
+    for paths in (1000, 10000, 100000):
+        for place, k in ((N.SDD_PLACE_ALL, 0), (N.SDD_PLACE_EQUISPACED, 7), (N.SDD_PLACE_EXTREMA, 0)):
+            spec = W.MeshSpec(sx=2, sy=2, paths=paths, **base)
+            with N.Plan(spec) as P:
+                N.sdd_plan_set_placement(P.handle, place, k)
+                mesh = np.zeros((29, 29, 2))
+                ms, ss = N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), mesh)
+                q = N.sdd_mesh_quality(P.handle, mesh, ref)
+                _, n_mc = N.sdd_plan_placement(P.handle)
+            rows.append({"N": paths, "placement": ["all", "7 equispaced", "extrema"][place],
+                         "mc_nodes": n_mc, "q_max": q["q_max"], "q_mean": q["q_mean"],
+                         "r_max": q["r_max"], "r_mean": q["r_mean"], "l_inf": q["l_inf"],
+                         "folds": q["folds"], "path_steps": int(ms.path_steps)})
+    print(json.dumps({"metric": "mesh quality vs single-domain mesh",
+                      "workload": "running example, 29x29, 2x2, 1D boundary map, dt=%g, bridge exit test"
+                                  % args.quality_dt,
+                      "single_domain": {"q_max": q_ref["q_max"], "q_mean": q_ref["q_mean"]},
+                      "rows": rows}))
+    return 0
+
+
 def achieved_steps_per_s(path_steps, seconds):
     return path_steps / seconds
 
@@ -553,6 +595,9 @@ def main(argv=None):
     ap.add_argument("--sample-paths", type=int, default=4096)
     ap.add_argument("--no-full", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--quality-report", action="store_true",
+                    help="mesh quality of DD and few-point meshes on the running example")
+    ap.add_argument("--quality-dt", type=float, default=1e-4)
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
     ap.add_argument("--n-max", type=int, default=1025)
     ap.add_argument("--target-stderr", type=float, default=1e-3)
@@ -575,6 +620,8 @@ def main(argv=None):
         return run_serve(args)
     if args.precision_report:
         return run_precision(args)
+    if args.quality_report:
+        return run_quality(args)
     if args.config == "config3":
         return run_batched(args)
     return run_native(args)
