@@ -23,6 +23,9 @@ Parts (each follows the passage it cites):
   with c at edge midpoints; subdomains take the interface values as Dirichlet
   data (§2.1, §3.5).  The linear solve is scipy's sparse direct solver.
 * ``closed_form_1d`` and ``torsion_exit_time``: the exact solutions used as pins.
+* ``perona_malik``: FTCS anisotropic smoothing of a mesh (§3.5).
+* ``cell_quality`` / ``mesh_quality``: Q(K), R_max, R_mean, l_inf (§3.1, §3.3);
+  ``placement`` / ``interpolate_interface``: few-point interfaces (§3.6).
 """
 from __future__ import annotations
 
@@ -440,6 +443,34 @@ def torsion_exit_time(s: float, t: float, terms: int = 401) -> float:
     terms_ = 16.0 * np.sin(M * math.pi * s) * np.sin(K * math.pi * t) / (
         math.pi ** 4 * M * K * (M * M + K * K))
     return float(terms_.sum())
+
+
+# ---------------------------------------------------- mesh smoothing -----
+def perona_malik(U: np.ndarray, steps: int, dt: float, k: float) -> np.ndarray:
+    """Anisotropic (Perona-Malik) smoothing of a mesh U[j, i, comp] (§3.5,
+    eq. PeronaMalikDiffusion): `steps` forward-Euler, centred-in-space (FTCS)
+    steps of length dt of u_t = div(g grad u) for each component separately,
+    g = exp(-|grad u|^2 / k^2).  The conductance of each of a node's four
+    edges comes from that edge's own difference, g(|u_nb - u| / h) (Perona
+    and Malik's discrete scheme); boundary values stay fixed:
+      u <- u + dt/h^2 sum_{nb in E,W,N,S} g(|u_nb - u| / h) (u_nb - u)."""
+    U = np.array(U, dtype=np.float64, copy=True)
+    n = U.shape[0]
+    h = 1.0 / (n - 1)
+    r = dt / (h * h)
+
+    def flux(d):
+        return np.exp(-(d / h) ** 2 / (k * k)) * d
+
+    for _ in range(steps):
+        V = U.copy()
+        for c in range(2):
+            u = U[:, :, c]
+            mid = u[1:-1, 1:-1]
+            V[1:-1, 1:-1, c] = mid + r * (flux(u[1:-1, 2:] - mid) + flux(u[1:-1, :-2] - mid)
+                                          + flux(u[2:, 1:-1] - mid) + flux(u[:-2, 1:-1] - mid))
+        U = V
+    return U
 
 
 # ------------------------------------------------------- mesh quality -----
