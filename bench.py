@@ -33,12 +33,30 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 # Algorithmic arithmetic operations of one FP32 path-step of the ring
-# density, counted per thread ("Roofline of the path kernel"):
+# density, counted per thread:
 #   Philox4x32-10 / 2 steps: 10 rounds x (2 wide multiplies counted as 2,
 #   2 three-input xors, 2 key additions) = 60 -> 30 per step
 #   two uniforms (shift-or + add): 4;  Box-Muller pair: 10;  ring drift: 22;
 #   Euler-Maruyama update: 4;  exit test: 6;  step count and cap test: 2
 OPS_PER_STEP_RING_FP32 = 30 + 4 + 10 + 22 + 4 + 6 + 2        # = 78
+# Exponential time stepping adds per step: half a Philox block for the two
+# step lengths (30), one uniform (2), -log2 U with its clamp and the scale by
+# ln 2 (3), the length into the noise scale (1) and into the drift (1).
+OPS_EXPO_EXTRA = 30 + 2 + 3 + 1 + 1                           # = 37
+# The Brownian-bridge test adds the distance test of a step pair's three
+# points (9 per pair); with exponential steps also the pair's largest length
+# into sqrt(23 h) (3 per pair).
+OPS_BRIDGE_EXTRA = 4.5
+OPS_BRIDGE_EXPO_EXTRA = 1.5
+
+
+def ops_per_step(stepper: int, exit_test: int) -> float:
+    ops = float(OPS_PER_STEP_RING_FP32)
+    if stepper == W.STEP_EXPONENTIAL:
+        ops += OPS_EXPO_EXTRA
+    if exit_test == W.EXIT_BRIDGE:
+        ops += OPS_BRIDGE_EXTRA + (OPS_BRIDGE_EXPO_EXTRA if stepper == W.STEP_EXPONENTIAL else 0)
+    return ops
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -125,6 +143,28 @@ def make_spec(name: str):
     raise ValueError(name)
 
 
+def bench_spec(args, seed=None):
+    """The workload of a single-mesh run with the command line's overrides
+    (paths, mean step, stepper, exit test; `seed` for a replica's own seed)."""
+    spec = make_spec(args.config)
+    over = {}
+    if seed is not None:
+        over["seed"] = seed
+    if args.paths:
+        over["paths"] = args.paths
+    if args.dt:
+        over["dt"] = args.dt
+    if args.stepper == "exponential":
+        over["stepper"] = W.STEP_EXPONENTIAL
+    if args.exit_test == "bridge":
+        over["exit_test"] = W.EXIT_BRIDGE
+    spec = W.MeshSpec(**{**spec.__dict__, **over})
+    if spec.stepper != W.STEP_EULER or spec.exit_test != W.EXIT_END_OF_STEP or args.dt:
+        spec = W.MeshSpec(**{**spec.__dict__, "label": "%s, %s steps, %s exit test, dt=%g" % (
+            spec.label.split(" N=")[0], args.stepper, args.exit_test, spec.dt)})
+    return spec
+
+
 # ------------------------------------------------------------ CPU oracle ----
 def oracle_sample(spec, budget_s: float = 15.0, threads: int | None = None):
     """Times the FP64 oracle on a bounded sample of `spec`: evenly spaced
@@ -138,15 +178,14 @@ def oracle_sample(spec, budget_s: float = 15.0, threads: int | None = None):
     idx = np.linspace(0, len(nodes) - 1, k).round().astype(int)
     # calibration: 32 paths per sampled node
     t0 = time.perf_counter()
+    kw = dict(node_ids=idx, threads=threads, exit_test=spec.exit_test, stepper=spec.stepper)
     r = oracle.mc_nodes(spec.n, nodes[idx], E, spec.family, spec.coef_mode, spec.params,
-                        spec.seed, 32, spec.dt, spec.cap(), spec.tie(), node_ids=idx,
-                        threads=threads)
+                        spec.seed, 32, spec.dt, spec.cap(), spec.tie(), **kw)
     cal = time.perf_counter() - t0
     paths = int(max(32, min(spec.paths, 32 * budget_s / max(cal, 1e-3))))
     t0 = time.perf_counter()
     r = oracle.mc_nodes(spec.n, nodes[idx], E, spec.family, spec.coef_mode, spec.params,
-                        spec.seed, paths, spec.dt, spec.cap(), spec.tie(), node_ids=idx,
-                        threads=threads)
+                        spec.seed, paths, spec.dt, spec.cap(), spec.tie(), **kw)
     el = time.perf_counter() - t0
     steps = int(r["steps"].sum())
     return {"value": steps / el, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
@@ -160,7 +199,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    spec = make_spec(args.config)
+    spec = bench_spec(args)
     threads = oracle.default_threads()
     for _ in range(args.warmup):
         oracle_sample(spec, budget_s=2.0, threads=threads)
@@ -196,13 +235,9 @@ def run_native(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = make_spec(args.config)
     # independent problem per rank: its own seed (weak scaling, no collective)
     from paper_1310_3435_gb300 import replicas
-    over = {"seed": replicas.rank_seed(spec.seed, rank)}
-    if args.paths:
-        over["paths"] = args.paths
-    spec = W.MeshSpec(**{**spec.__dict__, **over})
+    spec = bench_spec(args, seed=replicas.rank_seed(make_spec(args.config).seed, rank))
     stream = torch.cuda.Stream(device=dev)
     plan = N.Plan(spec)
     mc = plan.mc_params(precision=spec.precision if args.precision is None else args.precision,
@@ -286,7 +321,8 @@ def run_native(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * 128 * sm_clock_max * 1e6 / 1e9          # Gop/s
     t_mc = sum(ms_mc) / len(ms_mc) / 1000.0
-    achieved = OPS_PER_STEP_RING_FP32 * path_steps / t_mc / 1e9
+    ops = ops_per_step(spec.stepper, spec.exit_test)
+    achieved = ops * path_steps / t_mc / 1e9
     line = {
         "mc_path_steps_per_s": achieved_steps_per_s(path_steps, t_mc),
         "metric": "SDE path-steps/s",
@@ -298,18 +334,20 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": spec.label, "n": n, "split": [spec.sx, spec.sy],
                    "interface_nodes": plan.n_nodes, "paths_per_node": spec.paths,
-                   "dt": spec.dt, "path_steps_per_mesh": path_steps,
+                   "dt": spec.dt, "stepper": args.stepper, "exit_test": args.exit_test,
+                   "path_steps_per_mesh": path_steps,
                    "l2": "flushed between timed steps (2x L2 write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "meshes_per_s": meshes_per_s,
         "ms_interface_mc": float(np.mean(ms_mc)), "ms_subdomain_solve": float(np.mean(ms_solve)),
         "max_stderr": float(mc_stats.max_stderr),
+        "non_exits": int(mc_stats.non_exits),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
                      "frac": achieved / alu_peak, "traffic": None,
                      "kernel": "k_paths<FP32> (+k_reduce)",
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                                    % (sms, sm_clock_max, peak_kind),
-                     "ops_per_path_step": OPS_PER_STEP_RING_FP32},
+                     "ops_per_path_step": ops},
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
@@ -512,42 +550,71 @@ def run_precision(args):
 def run_quality(args):
     """Mesh-quality report on the paper's running example (eq.
     MonitorFunctionRunningExample: rho = 1 + 15 exp(-50 (x - 3/4)^2 - 50 (y -
-    1/2)^2 - 1/2), generator coefficient 1/rho, 29 x 29 grid): the 2 x 2
-    stochastic-deterministic DD mesh against the single-domain mesh (R_max,
-    R_mean, l_inf as in §3.3, §3.5), for several N, and few-point interfaces
-    with 7 equispaced points per line against the extrema placement (§3.6).
-    Boundary map: the 1D generator on the sides (§3.2)."""
+    1/2)^2 - 1/2), generator coefficient 1/rho, 29 x 29 grid, the 1D generator
+    on the sides as boundary map, §3.2), with exponential time stepping and
+    the boundary test as in the paper's experiments.  Against the
+    single-domain mesh (Q_max, Q_mean, R_max, R_mean, l_inf; §3.1, §3.3):
+      * the fully probabilistic mesh (§3.4) at lambda = 1000, N = 1000 and
+        10000, and the N = 1000 mesh after m = 1, 2, 5, 10 Perona-Malik steps
+        (dt = 1e-4, k = 1000, §3.5; the reference smoothed alike);
+      * the 2 x 2 stochastic-deterministic mesh at lambda = 1 / quality-dt,
+        N = 1e3, 1e4, 1e5, with every interface node, 7 equispaced points per
+        line, or the extrema placement (§3.5, §3.6)."""
     import torch
     from paper_1310_3435_gb300 import native as N
     torch.cuda.set_device(0)
+    n = 29
     rho = W.bumps((15.0 * math.exp(-0.5), 0.75, 0.5, 50.0, 50.0))
-    base = dict(n=29, family=W.FAMILY_BUMPS, params=rho, coef_mode=W.COEF_INV_W,
-                bmap_mode=W.BMAP_PAPER_1D, dt=args.quality_dt, seed=0, precision=W.FP32_STEP, exit_test=W.EXIT_BRIDGE,
-                solver=W.SOLVER_SOR, tol=1e-12)
-    single = W.MeshSpec(sx=1, sy=1, paths=2, **base)
+    base = dict(n=n, family=W.FAMILY_BUMPS, params=rho, coef_mode=W.COEF_INV_W,
+                bmap_mode=W.BMAP_PAPER_1D, seed=0, precision=W.FP32_STEP,
+                exit_test=W.EXIT_BRIDGE, stepper=W.STEP_EXPONENTIAL, solver=W.SOLVER_SOR,
+                tol=1e-12)
+    single = W.MeshSpec(sx=1, sy=1, paths=2, dt=1e-3, **base)
     with N.Plan(single) as P:
-        ref = np.zeros((29, 29, 2))
+        ref = np.zeros((n, n, 2))
         N.sdd_subdomain_solve(P.handle, np.zeros((0, 2)), P.solve_params(), ref)
         q_ref = N.sdd_mesh_quality(P.handle, ref)
-    rows = []
+
+    def row(P, mesh, against, **extra):
+        q = N.sdd_mesh_quality(P.handle, mesh, against)
+        out = dict(extra)
+        out.update({k: q[k] for k in ("q_max", "q_mean", "ref_q_max", "ref_q_mean", "r_max",
+                                      "r_mean", "l_inf", "folds")})
+        return out
+
+    full = []
+    for paths in (1000, 10000):
+        spec = W.MeshSpec(sx=n - 1, sy=n - 1, paths=paths, dt=1e-3, **base)
+        with N.Plan(spec) as P:
+            mesh = np.zeros((n, n, 2))
+            ms, _ = N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), mesh)
+            full.append(row(P, mesh, ref, N=paths, m=0, path_steps=int(ms.path_steps)))
+            if paths == 1000:
+                for m in (1, 2, 5, 10):
+                    sm, rs = mesh.copy(), ref.copy()
+                    N.sdd_mesh_smooth(P.handle, sm, m, 1e-4, 1000.0)
+                    N.sdd_mesh_smooth(P.handle, rs, m, 1e-4, 1000.0)
+                    full.append(row(P, sm, rs, N=paths, m=m))
+    dd = []
     for paths in (1000, 10000, 100000):
-        for place, k in ((N.SDD_PLACE_ALL, 0), (N.SDD_PLACE_EQUISPACED, 7), (N.SDD_PLACE_EXTREMA, 0)):
-            spec = W.MeshSpec(sx=2, sy=2, paths=paths, **base)
+        for place, k in ((N.SDD_PLACE_ALL, 0), (N.SDD_PLACE_EQUISPACED, 7),
+                         (N.SDD_PLACE_EXTREMA, 0)):
+            spec = W.MeshSpec(sx=2, sy=2, paths=paths, dt=args.quality_dt, **base)
             with N.Plan(spec) as P:
                 N.sdd_plan_set_placement(P.handle, place, k)
-                mesh = np.zeros((29, 29, 2))
-                ms, ss = N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), mesh)
-                q = N.sdd_mesh_quality(P.handle, mesh, ref)
+                mesh = np.zeros((n, n, 2))
+                ms, _ = N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), mesh)
                 _, n_mc = N.sdd_plan_placement(P.handle)
-            rows.append({"N": paths, "placement": ["all", "7 equispaced", "extrema"][place],
-                         "mc_nodes": n_mc, "q_max": q["q_max"], "q_mean": q["q_mean"],
-                         "r_max": q["r_max"], "r_mean": q["r_mean"], "l_inf": q["l_inf"],
-                         "folds": q["folds"], "path_steps": int(ms.path_steps)})
+                dd.append(row(P, mesh, ref, N=paths,
+                              placement=["all", "7 equispaced", "extrema"][place],
+                              mc_nodes=n_mc, path_steps=int(ms.path_steps)))
     print(json.dumps({"metric": "mesh quality vs single-domain mesh",
-                      "workload": "running example, 29x29, 2x2, 1D boundary map, dt=%g, bridge exit test"
-                                  % args.quality_dt,
+                      "workload": "running example, 29x29, 1D boundary map, exponential steps "
+                                  "with the boundary test",
                       "single_domain": {"q_max": q_ref["q_max"], "q_mean": q_ref["q_mean"]},
-                      "rows": rows}))
+                      "fully_probabilistic": {"lambda": 1000, "smoothing": "dt=1e-4, k=1000",
+                                              "rows": full},
+                      "dd_2x2": {"lambda": 1.0 / args.quality_dt, "rows": dd}}))
     return 0
 
 
@@ -598,6 +665,10 @@ def main(argv=None):
     ap.add_argument("--quality-report", action="store_true",
                     help="mesh quality of DD and few-point meshes on the running example")
     ap.add_argument("--quality-dt", type=float, default=1e-4)
+    ap.add_argument("--stepper", choices=["euler", "exponential"], default="euler",
+                    help="time stepping of the paths (exponential: mean step dt)")
+    ap.add_argument("--exit-test", choices=["end", "bridge"], default="end")
+    ap.add_argument("--dt", type=float, default=0.0, help="override the workload's (mean) step")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
     ap.add_argument("--n-max", type=int, default=1025)
     ap.add_argument("--target-stderr", type=float, default=1e-3)

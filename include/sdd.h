@@ -99,6 +99,19 @@ extern "C" {
 #define SDD_EXIT_END_OF_STEP 0
 #define SDD_EXIT_BRIDGE      1
 
+/* time stepping of the paths (§2.2):
+ *   EULER       : Euler-Maruyama with the constant step dt
+ *   EXPONENTIAL : exponential time stepping (after Jansons and Lythe): step k
+ *                 has the random length h = dt E, E = -ln U a unit-mean
+ *                 exponential (density lambda exp(-lambda h), lambda = 1/dt),
+ *                 U from words 0 and 1 of Philox counter (k/2, path, node, 2)
+ *                 for steps k, k+1 (k even); the update is the Euler-Maruyama
+ *                 one with step h, and the Brownian-bridge test (with
+ *                 SDD_EXIT_BRIDGE) uses h in place of dt.  dt is the mean
+ *                 step 1/lambda; the default step cap stays ceil(2/dt). */
+#define SDD_STEP_EULER       0
+#define SDD_STEP_EXPONENTIAL 1
+
 /* few-point interface (§3.6): where the Monte Carlo estimate is computed; the
  * other interface nodes are interpolated linearly along their interface line
  * between the nearest Monte Carlo nodes or the line's boundary ends
@@ -134,7 +147,8 @@ typedef struct {
 
 typedef struct {
     uint64_t paths_per_node;           /* N >= 2, < 2^32 */
-    double dt;                         /* Euler-Maruyama step, > 0 */
+    double dt;                         /* Euler-Maruyama step (mean step with
+                                          SDD_STEP_EXPONENTIAL), > 0 */
     uint64_t seed;                     /* Philox4x32-10 key (lo, hi words) */
     int32_t precision;                 /* SDD_FP64 | SDD_FP32_STEP */
     int32_t chunk;                     /* paths per work item: 0 = automatic, else a
@@ -142,7 +156,7 @@ typedef struct {
     uint64_t max_steps;                /* step cap per path, 0 = ceil(2/dt) */
     double tie_delta;                  /* <0: default (1e-11 FP64, 0 FP32) */
     int32_t exit_test;                 /* SDD_EXIT_END_OF_STEP | SDD_EXIT_BRIDGE */
-    int32_t reserved;
+    int32_t stepper;                   /* SDD_STEP_EULER | SDD_STEP_EXPONENTIAL */
 } sdd_mc_params;
 
 typedef struct {
@@ -188,6 +202,9 @@ typedef struct {
  * density `dens` and boundary map `bmap`: enumerates the interface nodes,
  * builds the boundary tables and copies them to the current device.
  * Requires 3 <= n <= 16385, 1 <= sx, sy <= n-1.  *out receives the plan.
+ * sx = sy = n-1 gives the fully probabilistic mesh (§3.4): every interior
+ * grid line is an interface, so every interior node is a Monte Carlo node
+ * ((n-2)^2 of them) and every subdomain is one empty cell.
  * Errors: INVALID_ARG (sizes, unknown family/mode, nb > SDD_MAX_BUMPS, NULL),
  * OOM, CUDA, NO_DEVICE.  Paper: §2.1, Fig. 1 (interfaces); §3.2 (boundary map). */
 int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap* bmap,
@@ -269,6 +286,19 @@ typedef struct {
  * Synchronises `stream`. */
 int sdd_mesh_quality(sdd_plan* plan, const double* mesh, const double* ref, sdd_quality* out,
                      void* stream);
+
+/* Anisotropic (Perona-Malik) smoothing of a mesh (§3.5, eq.
+ * PeronaMalikDiffusion): `steps` forward-Euler, centred-in-space (FTCS) steps
+ * of length dt of u_t = div(g grad u) for each component, g =
+ * exp(-|grad u|^2 / k^2).  Each of a node's four edges conducts with g of its
+ * own difference over h = 1/(n-1) (Perona and Malik's discrete scheme):
+ *   u <- u + dt/h^2 sum_{E,W,N,S} g(|u_nb - u| / h) (u_nb - u);
+ * boundary values stay fixed.  mesh: [n][n][2] of the plan's grid, host or
+ * device memory, smoothed in place (host: the call synchronises `stream`;
+ * device: stream-ordered).  One kernel launch per step.  Errors: INVALID_ARG
+ * (NULL, steps < 0, dt or k not positive and finite, dt/h^2 > 1/4, where the
+ * FTCS step loses its maximum principle), OOM, CUDA. */
+int sdd_mesh_smooth(sdd_plan* plan, double* mesh, int steps, double dt, double k, void* stream);
 
 /* Copies the plan's last results: mesh [n][n][2] (after a solve), interface
  * means and standard errors [n_nodes][2] (after a Monte Carlo call or a batch

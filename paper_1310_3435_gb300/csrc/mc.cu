@@ -137,6 +137,20 @@ __device__ __forceinline__ void box_muller_f32_step(uint32_t ra, uint32_t rb, fl
     sz = sin_approx(ang);
 }
 
+// Exponential time stepping (§2.2): the lengths of steps k, k+1 (k even) are
+// dt E with E = -ln U, U from words 0 and 1 of Philox counter
+// (k/2, path, node, 2).  FP64: U = (r + 1/2) 2^-32.  FP32: returns
+// E / ln 2 = -log2 U with the FP32 uniform, clamped at 0 (the approximate
+// log2 of a U next to 1 may land on the wrong side of 0).
+__device__ __forceinline__ double exp_unit_f64(uint32_t r)
+{
+    return -log(((double)r + 0.5) * 0x1p-32);
+}
+__device__ __forceinline__ float exp_unit_log2_f32(uint32_t r)
+{
+    return fmaxf(-lg2_approx(uniform23(r)), 0.0f);
+}
+
 // Box-Muller, FP64 with CUDA's double-precision log / sqrt / sincospi.
 __device__ __forceinline__ void box_muller_f64(uint32_t ra, uint32_t rb, double& z0, double& z1)
 {
@@ -151,8 +165,10 @@ __device__ __forceinline__ void box_muller_f64(uint32_t ra, uint32_t rb, double&
 
 // ----------------------------------------------------- densities, FP32 ----
 // Each FP32 density gives the drift half of an Euler-Maruyama step:
-// advance(s, t) = (s, t) + b dt with b = grad ln c = sgn grad(w)/w (c = w^sgn),
-// dt folded into the last multiplication.
+// advance(s, t, f) = (s, t) + b f dt with b = grad ln c = sgn grad(w)/w
+// (c = w^sgn), f dt folded into the last multiplication; f = 1 for constant
+// steps (the multiplication by the constant 1 folds away), f = h/dt for a
+// step of length h (exponential time stepping).
 // BUMPS: pf[8b..8b+6] = A, cs, ct, ks log2 e, kt log2 e, -2 ks, -2 kt.
 template <int NB>
 struct BumpsF32 {
@@ -167,7 +183,8 @@ struct BumpsF32 {
             for (int q = 0; q < 7; ++q) p[b][q] = M.pf[8 * b + q];
         sdt = (float)(M.sgn * M.dt);
     }
-    __device__ __forceinline__ void advance(float s, float t, float& as, float& at) const
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at,
+                                            float fdt = 1.0f) const
     {
         float w = 1.0f, gs = 0.0f, gt = 0.0f;
 #pragma unroll
@@ -179,7 +196,7 @@ struct BumpsF32 {
             gs = fmaf(e * p[b][5], ds, gs);
             gt = fmaf(e * p[b][6], dtt, gt);
         }
-        const float inv = sdt * rcp_approx(w);
+        const float inv = (sdt * fdt) * rcp_approx(w);
         as = fmaf(gs, inv, s);
         at = fmaf(gt, inv, t);
     }
@@ -196,7 +213,8 @@ struct RingF32 {
         cs = M.pf[0]; ct = M.pf[1]; r0 = M.pf[2]; c1 = M.pf[3]; A4 = M.pf[4];
         Kdt = (float)((double)M.pf[5] * M.dt);
     }
-    __device__ __forceinline__ void advance(float s, float t, float& as, float& at) const
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at,
+                                            float fdt = 1.0f) const
     {
         const float ds = s - cs, dtt = t - ct;
         const float r2 = fmaf(ds, ds, dtt * dtt);
@@ -206,7 +224,7 @@ struct RingF32 {
         const float ope = 1.0f + e;
         const float D = ope * fmaf(ope, ope, A4 * e);
         const float num = copysignf(fmaf(-e, e, e), u) * rinv;
-        const float f = (Kdt * num) * rcp_approx(D);
+        const float f = ((Kdt * fdt) * num) * rcp_approx(D);
         as = fmaf(f, ds, s);
         at = fmaf(f, dtt, t);
     }
@@ -223,14 +241,15 @@ struct RidgeF32 {
         A = M.pf[0]; kl = M.pf[1]; t0 = M.pf[2]; a = M.pf[3]; f = M.pf[4];
         m2k = M.pf[5]; m2paf = M.pf[6]; sdt = (float)(M.sgn * M.dt);
     }
-    __device__ __forceinline__ void advance(float s, float t, float& as, float& at) const
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at,
+                                            float fdt = 1.0f) const
     {
         const float fr = f * s;
         const float x = TWO_PI_F * (fr - rintf(fr));           // in [-pi, pi]
         const float sn = sin_approx(x), cn = cos_approx(x);
         const float v = t - t0 - a * sn;
         const float e = A * ex2_approx(-kl * v * v);
-        const float inv = sdt * rcp_approx(1.0f + e);
+        const float inv = (sdt * fdt) * rcp_approx(1.0f + e);
         const float gt = e * m2k * v;
         at = fmaf(gt, inv, t);
         as = fmaf(gt * (m2paf * cn), inv, s);
@@ -532,18 +551,20 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
     __syncwarp();
 
     const bool bridge = M.bridge != 0;
+    const bool expo = M.stepper == SDD_STEP_EXPONENTIAL;
     const R inv_dt = R(1) / dtR, qmax = R(23) * dtR;
     int bedge = -1;
     R btau = R(0);
 
-    // One Euler-Maruyama step from (xs, xt) with normals (za, zb) into
-    // (ys, yt).  Returns 0 to continue, 1 on exit through the end point, 2 at
-    // the step cap, 3 on a Brownian-bridge crossing (edge bedge, btau).
-    auto step = [&](R za, R zb, bool check_cap) -> int {
+    // One Euler-Maruyama step of length h from (xs, xt) with normals (za, zb)
+    // into (ys, yt).  Returns 0 to continue, 1 on exit through the end point,
+    // 2 at the step cap, 3 on a Brownian-bridge crossing (edge bedge, btau).
+    auto step = [&](R za, R zb, R h, bool check_cap) -> int {
         R bs, bt;
         dens.drift(xs, xt, bs, bt);
-        ys = xs + bs * dtR + sq * za;
-        yt = xt + bt * dtR + sq * zb;
+        const R sqh = expo ? sqrt(R(2) * h) : sq;
+        ys = xs + bs * h + sqh * za;
+        yt = xt + bt * h + sqh * zb;
         ++k;
         if constexpr (PREC == SDD_FP64) {
             const R m = fmin(fmin(fabs(ys), fabs(R(1) - ys)), fmin(fabs(yt), fabs(R(1) - yt)));
@@ -551,7 +572,8 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
         }
         if ((ys <= R(0)) | (ys >= R(1)) | (yt <= R(0)) | (yt >= R(1))) return 1;
         if (bridge) {
-            bedge = bridge_exit<R>(xs, xt, ys, yt, inv_dt, qmax, philox, k - 1u, path, nid, btau, tie);
+            bedge = bridge_exit<R>(xs, xt, ys, yt, expo ? R(1) / h : inv_dt,
+                                   expo ? R(23) * h : qmax, philox, k - 1u, path, nid, btau, tie);
             if (bedge >= 0) return 3;
         }
         if (check_cap && k >= kmax) return 2;
@@ -572,13 +594,24 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
                 box_muller_f32(r.x, r.y, z0, z1);
                 box_muller_f32(r.z, r.w, z2, z3);
             }
+            R h0 = dtR, h1 = dtR;
+            if (expo) {
+                const uint4 L = philox(make_uint4(k >> 1, path, nid, 2u));
+                if constexpr (PREC == SDD_FP64) {
+                    h0 = dtR * exp_unit_f64(L.x);
+                    h1 = dtR * exp_unit_f64(L.y);
+                } else {
+                    h0 = dtR * (exp_unit_log2_f32(L.x) * 0.69314718055994530942f);
+                    h1 = dtR * (exp_unit_log2_f32(L.y) * 0.69314718055994530942f);
+                }
+            }
             if (k + 2u <= kmax) {
-                ended = step(z0, z1, false);
-                if (!ended) ended = step(z2, z3, false);
+                ended = step(z0, z1, h0, false);
+                if (!ended) ended = step(z2, z3, h1, false);
                 if (!ended && k >= kmax) ended = 2;
             } else {
-                ended = step(z0, z1, true);
-                if (!ended) ended = step(z2, z3, true);
+                ended = step(z0, z1, h0, true);
+                if (!ended) ended = step(z2, z3, h1, true);
             }
             if (ended) {
                 R tau = btau;                      // bridge crossing: edge and point known
@@ -806,7 +839,7 @@ __device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs
 // Streams the items of mesh M starting at `first` (already taken from the
 // queue).  Returns the first item taken that is not M's (the next mesh's, or
 // >= total_items when the queue is exhausted).
-template <class Dens, class Keys>
+template <bool EXPO, class Dens, class Keys>
 __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const Dens& dens,
                                                          const Keys& philox,
                                                          unsigned long long first,
@@ -835,6 +868,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     const bool bridge = M.bridge != 0;
     const float inv_dt = (float)(1.0 / M.dt), qmax = (float)(23.0 * M.dt);
     const float dth = (float)std::sqrt(23.0 * M.dt);
+    constexpr float LN2F = 0.69314718055994530942f;
     float xs = 0.f, xt = 0.f;
     uint32_t k = 0, path = 0, node = 0, nid = 0;
     int set = 0;
@@ -890,22 +924,33 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
             } else {
                 r = philox(make_uint4(k >> 1, path, nid, 0u));
             }
+            // fa, fb: the steps' lengths over dt (1, or E = -ln U when the
+            // steps are exponential)
+            float fa = 1.0f, fb = 1.0f;
+            if constexpr (EXPO) {
+                const uint4 L = philox(make_uint4(k >> 1, path, nid, 2u));
+                fa = exp_unit_log2_f32(L.x) * LN2F;
+                fb = exp_unit_log2_f32(L.y) * LN2F;
+            }
             float na, ca, sa, nb, cb, sb;
-            box_muller_f32_step(r.x, r.y, c4dt, na, ca, sa);
-            box_muller_f32_step(r.z, r.w, c4dt, nb, cb, sb);
+            box_muller_f32_step(r.x, r.y, c4dt * fa, na, ca, sa);
+            box_muller_f32_step(r.z, r.w, c4dt * fb, nb, cb, sb);
             float as, at;
-            dens.advance(xs, xt, as, at);
+            dens.advance(xs, xt, as, at, fa);
             const float y1s = fmaf(na, ca, as), y1t = fmaf(na, sa, at);
-            dens.advance(y1s, y1t, as, at);
+            dens.advance(y1s, y1t, as, at, fb);
             const float y2s = fmaf(nb, cb, as), y2t = fmaf(nb, sb, at);
             // one test for both steps: every coordinate inside (0,1), and, with
             // the bridge test, every coordinate of x, y1, y2 farther than
-            // sqrt(23 dt) from the sides (no crossing probability to draw)?
+            // sqrt(23 h) from the sides (no crossing probability to draw)?
             const float lo = fminf(fminf(y1s, y1t), fminf(y2s, y2t));
             const float hi = fmaxf(fmaxf(y1s, y1t), fmaxf(y2s, y2t));
             bool fast = (lo > 0.f) & (hi < 1.f) & (k + 2u < kmax);
-            if (bridge)
-                fast = fast & (fminf(lo, fminf(xs, xt)) >= dth) & (fmaxf(hi, fmaxf(xs, xt)) <= 1.f - dth);
+            if (bridge) {
+                float d = dth;
+                if constexpr (EXPO) d = sqrt_approx(qmax * fmaxf(fa, fb));
+                fast = fast & (fminf(lo, fminf(xs, xt)) >= d) & (fmaxf(hi, fmaxf(xs, xt)) <= 1.f - d);
+            }
             if (fast) {
                 xs = y2s;
                 xt = y2t;
@@ -920,7 +965,9 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                 const bool out1 = (y1s <= 0.f) | (y1s >= 1.f) | (y1t <= 0.f) | (y1t >= 1.f);
                 if (out1) {
                     e = exit_edge<float>(xs, xt, y1s, y1t, tau);
-                } else if (bridge && (e = bridge_exit<float>(xs, xt, y1s, y1t, inv_dt, qmax, philox,
+                } else if (bridge && (e = bridge_exit<float>(xs, xt, y1s, y1t,
+                                                              EXPO ? inv_dt / fa : inv_dt,
+                                                              EXPO ? qmax * fa : qmax, philox,
                                                               k - 1u, path, nid, tau, dummy)) >= 0) {
                 } else if (k >= kmax) {
                     capped = true;
@@ -930,7 +977,9 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                     const bool out2 = (y2s <= 0.f) | (y2s >= 1.f) | (y2t <= 0.f) | (y2t >= 1.f);
                     if (out2) {
                         e = exit_edge<float>(y1s, y1t, y2s, y2t, tau);
-                    } else if (bridge && (e = bridge_exit<float>(y1s, y1t, y2s, y2t, inv_dt, qmax,
+                    } else if (bridge && (e = bridge_exit<float>(y1s, y1t, y2s, y2t,
+                                                                  EXPO ? inv_dt / fb : inv_dt,
+                                                                  EXPO ? qmax * fb : qmax,
                                                                   philox, k - 1u, path, nid, tau,
                                                                   dummy)) >= 0) {
                     } else if (k >= kmax) {
@@ -978,39 +1027,39 @@ __host__ __device__ __forceinline__ int fam_class(int family, int nb)
     return FC_BUMPS6;
 }
 
-template <int FC, class Keys>
+template <int FC, bool EXPO, class Keys>
 __device__ __forceinline__ unsigned long long stream_fc(const MeshDev& M, const Keys& keys,
                                                         unsigned long long item, const McArgs& a,
                                                         WarpAcc& W, int lane)
 {
-    if constexpr (FC == FC_RING) { RingF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_RIDGE) { RidgeF32 d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_BUMPS1) { BumpsF32<1> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_BUMPS2) { BumpsF32<2> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_BUMPS3) { BumpsF32<3> d; d.load(M); return run_stream(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_RING) { RingF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_RIDGE) { RidgeF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS1) { BumpsF32<1> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS2) { BumpsF32<2> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS3) { BumpsF32<3> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
     if constexpr (FC == FC_BUMPS6) {
         BumpsF32<SDD_MAX_BUMPS> d;
         d.load(M);
-        return run_stream(M, d, keys, item, a, W, lane);
+        return run_stream<EXPO>(M, d, keys, item, a, W, lane);
     }
     return a.total_items;
 }
 
-template <int FC, class Keys>
+template <int FC, bool EXPO, class Keys>
 __device__ __forceinline__ unsigned long long dispatch_stream(const MeshDev& M, const Keys& keys,
                                                               unsigned long long item,
                                                               const McArgs& a, WarpAcc& W, int lane)
 {
     if constexpr (FC != FC_ANY) {
-        return stream_fc<FC>(M, keys, item, a, W, lane);
+        return stream_fc<FC, EXPO>(M, keys, item, a, W, lane);
     } else {
         switch (fam_class(M.family, M.nb)) {
-            case FC_RING: return stream_fc<FC_RING>(M, keys, item, a, W, lane);
-            case FC_RIDGE: return stream_fc<FC_RIDGE>(M, keys, item, a, W, lane);
-            case FC_BUMPS1: return stream_fc<FC_BUMPS1>(M, keys, item, a, W, lane);
-            case FC_BUMPS2: return stream_fc<FC_BUMPS2>(M, keys, item, a, W, lane);
-            case FC_BUMPS3: return stream_fc<FC_BUMPS3>(M, keys, item, a, W, lane);
-            default: return stream_fc<FC_BUMPS6>(M, keys, item, a, W, lane);
+            case FC_RING: return stream_fc<FC_RING, EXPO>(M, keys, item, a, W, lane);
+            case FC_RIDGE: return stream_fc<FC_RIDGE, EXPO>(M, keys, item, a, W, lane);
+            case FC_BUMPS1: return stream_fc<FC_BUMPS1, EXPO>(M, keys, item, a, W, lane);
+            case FC_BUMPS2: return stream_fc<FC_BUMPS2, EXPO>(M, keys, item, a, W, lane);
+            case FC_BUMPS3: return stream_fc<FC_BUMPS3, EXPO>(M, keys, item, a, W, lane);
+            default: return stream_fc<FC_BUMPS6, EXPO>(M, keys, item, a, W, lane);
         }
     }
 }
@@ -1032,7 +1081,9 @@ __device__ __forceinline__ int find_mesh(const uint64_t* __restrict__ off, int n
 // ONE: single-mesh launch (record and round keys from the kernel parameters);
 // otherwise a batch (records in global memory, one key per mesh).  FC: the
 // density class the FP32 kernel is specialised for (FC_ANY: every class).
-template <int PREC, bool ONE, int FC>
+// EXPO: FP32 kernel with exponential time stepping (FP64 stepping reads the
+// stepper from the mesh record).
+template <int PREC, bool ONE, int FC, bool EXPO = false>
 __global__ void __launch_bounds__(MC_THREADS, PREC == SDD_FP64 ? SDD_MC_MIN_BLOCKS_F64 : SDD_MC_MIN_BLOCKS_F32)
 k_paths(const __grid_constant__ McArgs a)
 {
@@ -1077,10 +1128,10 @@ k_paths(const __grid_constant__ McArgs a)
             const MeshDev& M = ONE ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
             if constexpr (ONE) {
                 const ParamKeys keys{a.rk};
-                item = dispatch_stream<FC>(M, keys, item, a, W, lane);
+                item = dispatch_stream<FC, EXPO>(M, keys, item, a, W, lane);
             } else {
                 const RegKeys keys{M.key0, M.key1};
-                item = dispatch_stream<FC>(M, keys, item, a, W, lane);
+                item = dispatch_stream<FC, EXPO>(M, keys, item, a, W, lane);
             }
         }
     }
@@ -1236,58 +1287,70 @@ void fill_fp32_params(MeshDev& m, const sdd_density& d)
     }
 }
 
-// Kernel of a launch: precision, single mesh or batch, density class.
+// Kernel of a launch: precision, single mesh or batch, kernel class (density
+// class + KC_EXPO for exponential time stepping).
 using PathKernel = void (*)(McArgs);
 
-static PathKernel path_kernel(int precision, bool one, int fc)
+template <bool EXPO>
+static PathKernel path_kernel_fp32(bool one, int fc)
 {
-    if (precision == SDD_FP64) return one ? k_paths<SDD_FP64, true, FC_ANY> : k_paths<SDD_FP64, false, FC_ANY>;
     if (!one) {
         switch (fc) {
-            case FC_RING: return k_paths<SDD_FP32_STEP, false, FC_RING>;
-            case FC_RIDGE: return k_paths<SDD_FP32_STEP, false, FC_RIDGE>;
-            case FC_BUMPS1: return k_paths<SDD_FP32_STEP, false, FC_BUMPS1>;
-            case FC_BUMPS2: return k_paths<SDD_FP32_STEP, false, FC_BUMPS2>;
-            case FC_BUMPS3: return k_paths<SDD_FP32_STEP, false, FC_BUMPS3>;
-            case FC_BUMPS6: return k_paths<SDD_FP32_STEP, false, FC_BUMPS6>;
-            default: return k_paths<SDD_FP32_STEP, false, FC_ANY>;
+            case FC_RING: return k_paths<SDD_FP32_STEP, false, FC_RING, EXPO>;
+            case FC_RIDGE: return k_paths<SDD_FP32_STEP, false, FC_RIDGE, EXPO>;
+            case FC_BUMPS1: return k_paths<SDD_FP32_STEP, false, FC_BUMPS1, EXPO>;
+            case FC_BUMPS2: return k_paths<SDD_FP32_STEP, false, FC_BUMPS2, EXPO>;
+            case FC_BUMPS3: return k_paths<SDD_FP32_STEP, false, FC_BUMPS3, EXPO>;
+            case FC_BUMPS6: return k_paths<SDD_FP32_STEP, false, FC_BUMPS6, EXPO>;
+            default: return k_paths<SDD_FP32_STEP, false, FC_ANY, EXPO>;
         }
     }
     switch (fc) {
-        case FC_RING: return k_paths<SDD_FP32_STEP, true, FC_RING>;
-        case FC_RIDGE: return k_paths<SDD_FP32_STEP, true, FC_RIDGE>;
-        case FC_BUMPS1: return k_paths<SDD_FP32_STEP, true, FC_BUMPS1>;
-        case FC_BUMPS2: return k_paths<SDD_FP32_STEP, true, FC_BUMPS2>;
-        case FC_BUMPS3: return k_paths<SDD_FP32_STEP, true, FC_BUMPS3>;
-        default: return k_paths<SDD_FP32_STEP, true, FC_BUMPS6>;
+        case FC_RING: return k_paths<SDD_FP32_STEP, true, FC_RING, EXPO>;
+        case FC_RIDGE: return k_paths<SDD_FP32_STEP, true, FC_RIDGE, EXPO>;
+        case FC_BUMPS1: return k_paths<SDD_FP32_STEP, true, FC_BUMPS1, EXPO>;
+        case FC_BUMPS2: return k_paths<SDD_FP32_STEP, true, FC_BUMPS2, EXPO>;
+        case FC_BUMPS3: return k_paths<SDD_FP32_STEP, true, FC_BUMPS3, EXPO>;
+        default: return k_paths<SDD_FP32_STEP, true, FC_BUMPS6, EXPO>;
     }
 }
 
-int mesh_fam_class(int family, int nb) { return fam_class(family, nb); }
+static PathKernel path_kernel(int precision, bool one, int kc)
+{
+    if (precision == SDD_FP64) return one ? k_paths<SDD_FP64, true, FC_ANY> : k_paths<SDD_FP64, false, FC_ANY>;
+    const int fc = kc & (KC_EXPO - 1);
+    if (kc & KC_EXPO) return path_kernel_fp32<true>(one, fc);
+    return path_kernel_fp32<false>(one, fc);
+}
 
-int mc_grid_blocks(int precision, int fc, bool one, int* blocks, int* threads)
+int mesh_kernel_class(int family, int nb, int stepper)
+{
+    return fam_class(family, nb) + (stepper == SDD_STEP_EXPONENTIAL ? KC_EXPO : 0);
+}
+
+int mc_grid_blocks(int precision, int kc, bool one, int* blocks, int* threads)
 {
     int dev = 0, sms = 0, per_sm = 0;
     SDD_CUDA(cudaGetDevice(&dev));
     SDD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SDD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, reinterpret_cast<const void*>(path_kernel(precision, one, fc)), MC_THREADS, 0));
+        &per_sm, reinterpret_cast<const void*>(path_kernel(precision, one, kc)), MC_THREADS, 0));
     *blocks = sms * std::max(per_sm, 1);
     if (threads) *threads = MC_THREADS;
     return SDD_OK;
 }
 
-int launch_mc(const McArgs& args, int precision, int fc, cudaStream_t stream)
+int launch_mc(const McArgs& args, int precision, int kc, cudaStream_t stream)
 {
     if (args.total_items == 0) return SDD_OK;
     const bool one = args.meshes == nullptr;
     int blocks = 0, threads = 0;
-    int rc = mc_grid_blocks(precision, fc, one, &blocks, &threads);
+    int rc = mc_grid_blocks(precision, kc, one, &blocks, &threads);
     if (rc) return rc;
-    return launch_mc_sized(args, precision, fc, blocks, stream);
+    return launch_mc_sized(args, precision, kc, blocks, stream);
 }
 
-int launch_mc_sized(const McArgs& args, int precision, int fc, int blocks, cudaStream_t stream)
+int launch_mc_sized(const McArgs& args, int precision, int kc, int blocks, cudaStream_t stream)
 {
     if (args.total_items == 0) return SDD_OK;
     const bool one = args.meshes == nullptr;
@@ -1296,7 +1359,7 @@ int launch_mc_sized(const McArgs& args, int precision, int fc, int blocks, cudaS
     if ((uint64_t)blocks > max_blocks) blocks = (int)max_blocks;
     if (blocks < 1) blocks = 1;
     SDD_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
-    path_kernel(precision, one, fc)<<<blocks, threads, 0, stream>>>(args);
+    path_kernel(precision, one, kc)<<<blocks, threads, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
     const unsigned rb = (unsigned)((args.total_nodes + 255) / 256);

@@ -276,6 +276,8 @@ int validate_mc(const sdd_mc_params* mc)
         return fail(SDD_ERR_INVALID_ARG, "chunk must be 0 or a multiple of 32 up to 8192");
     if (mc->exit_test != SDD_EXIT_END_OF_STEP && mc->exit_test != SDD_EXIT_BRIDGE)
         return fail(SDD_ERR_INVALID_ARG, "unknown exit_test");
+    if (mc->stepper != SDD_STEP_EULER && mc->stepper != SDD_STEP_EXPONENTIAL)
+        return fail(SDD_ERR_INVALID_ARG, "unknown stepper");
     const double cap = mc->max_steps ? (double)mc->max_steps : std::ceil(2.0 / mc->dt);
     if (cap < 1.0 || cap > 4294967294.0)
         return fail(SDD_ERR_INVALID_ARG, "max_steps must be in [1, 2^32 - 2]");
@@ -303,6 +305,7 @@ void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
     m.chunks_per_node = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
     m.max_steps = (uint32_t)(mc->max_steps ? mc->max_steps : (uint64_t)std::ceil(2.0 / mc->dt));
     m.bridge = mc->exit_test == SDD_EXIT_BRIDGE ? 1 : 0;
+    m.stepper = mc->stepper;
     m.n_nodes = p->n_nodes;
     m.dt = mc->dt;
     m.sqrt2dt = std::sqrt(2.0 * mc->dt);
@@ -353,7 +356,7 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     a.queue = p->d_queue;
     a.slots = p->d_slots;
     SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
-    if ((rc = launch_mc(a, mc->precision, mesh_fam_class(m.family, m.nb), stream))) return rc;
+    if ((rc = launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper), stream))) return rc;
     if (few) {
         if ((rc = launch_interp(p->d_interp, (int64_t)p->h_interp.size(), stream))) return rc;
         const size_t bytes = (size_t)p->n_nodes * 2 * sizeof(double);
@@ -587,7 +590,7 @@ std::vector<InterpEntry> interp_entries(const sdd_plan* p, const std::vector<uin
 // be captured once into a CUDA graph and replayed.
 struct McGroup {
     int precision;
-    int fc;
+    int kc;                 // kernel class (density class + KC_EXPO)
     int blocks;                 // persistent grid
     McArgs args;
 };
@@ -655,7 +658,7 @@ int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
     if (phases & 1) {
         SDD_CUDA(cudaMemsetAsync(b->d_stats, 0, np * sizeof(McStatsDev), stream));
         for (const McGroup& g : b->groups) {
-            int rc = launch_mc_sized(g.args, g.precision, g.fc, g.blocks, stream);
+            int rc = launch_mc_sized(g.args, g.precision, g.kc, g.blocks, stream);
             if (rc) return rc;
         }
         int rc = launch_interp(b->d_interp, b->n_interp, stream);
@@ -1118,6 +1121,46 @@ int sdd_mesh_quality(sdd_plan* p, const double* mesh, const double* ref, sdd_qua
     return SDD_OK;
 }
 
+int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, void* stream_)
+{
+    clear_error();
+    if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (steps < 0) return fail(SDD_ERR_INVALID_ARG, "steps must be >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(k > 0.0) || !std::isfinite(k))
+        return fail(SDD_ERR_INVALID_ARG, "dt and k must be positive and finite");
+    const double h = 1.0 / (double)(p->n - 1);
+    if (dt / (h * h) > 0.25)
+        return fail(SDD_ERR_INVALID_ARG, "dt (n-1)^2 = " + std::to_string(dt / (h * h)) +
+                                             " exceeds 1/4: the FTCS step would be unstable");
+    int rc = check_device(p);
+    if (rc) return rc;
+    if (steps == 0) return SDD_OK;
+    cudaStream_t stream = as_stream(stream_);
+    const size_t count = 2 * (size_t)p->n * p->n;            // doubles of one mesh
+    const bool host = !is_device_ptr(mesh);
+    double* tmp = nullptr;
+    {
+        AllocOn on(stream);
+        if ((rc = dev_alloc(&tmp, (host ? 2 : 1) * count))) return rc;
+    }
+    double* u = host ? tmp + count : mesh;
+    if (host)
+        SDD_CUDA(cudaMemcpyAsync(u, mesh, count * sizeof(double), cudaMemcpyHostToDevice, stream));
+    rc = launch_smooth(p->n, u, tmp, steps, dt, k, stream);
+    if (rc) {
+        dev_free(tmp, stream);
+        return rc;
+    }
+    if (host) {
+        SDD_CUDA(cudaMemcpyAsync(mesh, u, count * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        dev_free(tmp, stream);
+        SDD_CUDA(cudaStreamSynchronize(stream));
+    } else {
+        dev_free(tmp, stream);
+    }
+    return SDD_OK;
+}
+
 int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* mc,
                      const sdd_solve_params* sp, sdd_batch** out)
 {
@@ -1153,11 +1196,11 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
             return rc;
         }
     }
-    // group meshes by (precision, density class); records in group order
+    // group meshes by (precision, kernel class); records in group order
     std::vector<std::pair<int, int>> key(n_plans);
     for (int i = 0; i < n_plans; ++i) {
         const int nb = plans[i]->dens.family == SDD_FAMILY_BUMPS ? (int)plans[i]->dens.params[0] : 0;
-        key[i] = {mc[i].precision, mesh_fam_class(plans[i]->dens.family, nb)};
+        key[i] = {mc[i].precision, mesh_kernel_class(plans[i]->dens.family, nb, mc[i].stepper)};
     }
     std::vector<int> order(n_plans);
     for (int i = 0; i < n_plans; ++i) order[i] = i;
@@ -1166,7 +1209,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
     std::vector<MeshDev> recs(n_plans);
     std::vector<uint64_t> offs;
     uint64_t slot_total = 0;
-    struct GInfo { int precision, fc, first, count; size_t item_off, node_off; uint64_t items, nodes, slot_base; };
+    struct GInfo { int precision, kc, first, count; size_t item_off, node_off; uint64_t items, nodes, slot_base; };
     std::vector<GInfo> gi;
     for (int k = 0; k < n_plans;) {
         int e = k;
@@ -1305,8 +1348,8 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         McGroup G;
         memset(&G, 0, sizeof(G));
         G.precision = g.precision;
-        G.fc = g.fc;
-        if ((rc = mc_grid_blocks(g.precision, g.fc, false, &G.blocks, nullptr))) {
+        G.kc = g.kc;
+        if ((rc = mc_grid_blocks(g.precision, g.kc, false, &G.blocks, nullptr))) {
             batch_free(b);
             return rc;
         }
@@ -1565,6 +1608,7 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
     m.chunks_per_node = (uint32_t)((mc->paths_per_node + chunk - 1) / chunk);
     m.max_steps = (uint32_t)(mc->max_steps ? mc->max_steps : (uint64_t)std::ceil(2.0 / mc->dt));
     m.bridge = mc->exit_test == SDD_EXIT_BRIDGE ? 1 : 0;
+    m.stepper = mc->stepper;
     m.n_nodes = n_nodes;
     m.dt = mc->dt;
     m.sqrt2dt = std::sqrt(2.0 * mc->dt);
@@ -1589,5 +1633,5 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
     a.queue = reinterpret_cast<unsigned long long*>(b);          // zeroed by the launcher
     a.slots = reinterpret_cast<Slot*>(b + kStaticHeadBytes);     // written before read
     SDD_CUDA(cudaMemsetAsync(m.stats, 0, sizeof(McStatsDev), stream));
-    return launch_mc(a, mc->precision, mesh_fam_class(m.family, m.nb), stream);
+    return launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper), stream);
 }

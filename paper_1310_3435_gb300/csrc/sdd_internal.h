@@ -48,7 +48,7 @@ struct MeshDev {
     uint32_t chunks_per_node;
     uint32_t max_steps;     // step cap per path (< 2^32)
     int32_t bridge;         // 1: Brownian-bridge exit test after each step
-    int32_t pad0;
+    int32_t stepper;        // SDD_STEP_EULER | SDD_STEP_EXPONENTIAL
     int64_t n_nodes;
     uint64_t item_begin;    // first work item of this mesh
     uint64_t node_begin;    // first global node of this mesh
@@ -99,10 +99,12 @@ struct McArgs {
     uint32_t rk[20];             // single mesh: Philox round keys (k0, k1) of rounds 0..9
 };
 
-// Density class of a mesh for the FP32 path kernel (one kernel per class);
-// kFamAny selects the kernel that handles every class.
-int mesh_fam_class(int family, int nb);
+// Kernel class of a mesh for the FP32 path kernel: its density class (one
+// kernel per class; kFamAny selects the kernel that handles every class) plus
+// KC_EXPO for exponential time stepping.  FP64 stepping has one kernel.
+int mesh_kernel_class(int family, int nb, int stepper);
 constexpr int kFamAny = 6;
+constexpr int KC_EXPO = 8;
 
 // Interpolated interface node of a few-point interface (§3.6): value =
 // (1 - w) A + w B per component, A / B the mean (and std-err) of interface
@@ -125,16 +127,21 @@ struct QualityDev {
 int launch_quality(int n, int family, const double* params, const double* u, const double* ref,
                    QualityDev* d_out, cudaStream_t stream);
 
-// Launches the path kernel (for density class `fc`) and the per-node
+// Perona-Malik smoothing of the mesh u [n][n][2] (device), `steps` FTCS steps
+// ping-ponged with `scratch` (device, same size); the result ends in u.
+int launch_smooth(int n, double* u, double* scratch, int steps, double dt, double k,
+                  cudaStream_t stream);
+
+// Launches the path kernel (for kernel class `kc`) and the per-node
 // reduction.
-int launch_mc(const McArgs& args, int precision, int fc, cudaStream_t stream);
+int launch_mc(const McArgs& args, int precision, int kc, cudaStream_t stream);
 
 // Same with a precomputed persistent-grid size (no device queries: usable
 // while a stream is being captured into a CUDA graph).
-int launch_mc_sized(const McArgs& args, int precision, int fc, int blocks, cudaStream_t stream);
+int launch_mc_sized(const McArgs& args, int precision, int kc, int blocks, cudaStream_t stream);
 
 // Persistent-grid size of the path kernel for the current device.
-int mc_grid_blocks(int precision, int fc, bool one, int* blocks, int* threads);
+int mc_grid_blocks(int precision, int kc, bool one, int* blocks, int* threads);
 
 // ------------------------------------------------------- solve records --
 struct SolveMeshDev {

@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "sdd_internal.h"
 
@@ -563,6 +564,38 @@ __global__ void __launch_bounds__(256) k_quality(QualityArgs a, const double2* _
     }
 }
 
+// Perona-Malik smoothing (§3.5, eq. PeronaMalikDiffusion), one FTCS step
+// u -> v per launch, both components: each of a node's four edges conducts
+// with g = exp(-(d/h)^2 / k^2) of its own difference d = u_nb - u, so
+//   v = u + r (g_E d_E + g_W d_W + g_N d_N + g_S d_S),  r = dt / h^2;
+// boundary nodes are copied.  One thread per node, mesh rows of double2.
+__device__ __forceinline__ double pm_flux(double d, double h, double k2)
+{
+    const double t = d / h;
+    return exp(-(t * t) / k2) * d;
+}
+
+__global__ void __launch_bounds__(256) k_pm_step(int n, const double2* __restrict__ u,
+                                                 double2* __restrict__ v, double h, double r,
+                                                 double k2)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (int64_t)n * n) return;
+    const int i = (int)(g % n), j = (int)(g / n);
+    const double2 c = u[g];
+    if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
+        v[g] = c;
+        return;
+    }
+    const double2 E = u[g + 1], Wn = u[g - 1], N = u[g + n], S = u[g - n];
+    double2 o;
+    o.x = c.x + r * (pm_flux(E.x - c.x, h, k2) + pm_flux(Wn.x - c.x, h, k2) +
+                     pm_flux(N.x - c.x, h, k2) + pm_flux(S.x - c.x, h, k2));
+    o.y = c.y + r * (pm_flux(E.y - c.y, h, k2) + pm_flux(Wn.y - c.y, h, k2) +
+                     pm_flux(N.y - c.y, h, k2) + pm_flux(S.y - c.y, h, k2));
+    v[g] = o;
+}
+
 }  // namespace
 
 int launch_quality(int n, int family, const double* params, const double* u, const double* ref,
@@ -579,6 +612,28 @@ int launch_quality(int n, int family, const double* params, const double* u, con
                                           reinterpret_cast<const double2*>(ref), d_out);
     SDD_CUDA(cudaGetLastError());
     count_launch();
+    return SDD_OK;
+}
+
+int launch_smooth(int n, double* u, double* scratch, int steps, double dt, double k,
+                  cudaStream_t stream)
+{
+    if (steps <= 0) return SDD_OK;
+    const double h = 1.0 / (double)(n - 1);
+    const double r = dt / (h * h), k2 = k * k;
+    const int64_t nodes = (int64_t)n * n;
+    const unsigned blocks = (unsigned)((nodes + 255) / 256);
+    double2* a = reinterpret_cast<double2*>(u);
+    double2* b = reinterpret_cast<double2*>(scratch);
+    for (int s = 0; s < steps; ++s) {
+        k_pm_step<<<blocks, 256, 0, stream>>>(n, a, b, h, r, k2);
+        SDD_CUDA(cudaGetLastError());
+        count_launch();
+        std::swap(a, b);
+    }
+    if (a != reinterpret_cast<double2*>(u))          // odd step count: result in scratch
+        SDD_CUDA(cudaMemcpyAsync(u, a, (size_t)nodes * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                 stream));
     return SDD_OK;
 }
 

@@ -34,6 +34,7 @@ SDD_BMAP_IDENTITY, SDD_BMAP_PAPER_1D, SDD_BMAP_TABLE = 0, 1, 2
 SDD_FP64, SDD_FP32_STEP = 0, 1
 SDD_SOLVER_SOR, SDD_SOLVER_CG_FP32_REFINE = 0, 1
 SDD_EXIT_END_OF_STEP, SDD_EXIT_BRIDGE = 0, 1
+SDD_STEP_EULER, SDD_STEP_EXPONENTIAL = 0, 1
 SDD_PLACE_ALL, SDD_PLACE_EQUISPACED, SDD_PLACE_EXTREMA = 0, 1, 2
 
 
@@ -59,7 +60,7 @@ class sdd_mc_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("max_steps", ctypes.c_uint64),
                 ("tie_delta", ctypes.c_double), ("exit_test", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("stepper", ctypes.c_int32)]
 
 
 class sdd_mc_stats(ctypes.Structure):
@@ -162,12 +163,13 @@ def load(build_if_missing: bool = True):
     L.sdd_plan_set_placement.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.sdd_plan_placement.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.sdd_mesh_quality.argtypes = [vp, vp, vp, P(sdd_quality), vp]
+    L.sdd_mesh_smooth.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
     for name in ("sdd_mesh_plan", "sdd_plan_num_nodes", "sdd_plan_nodes", "sdd_plan_edges",
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
                  "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
                  "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
                  "sdd_batch_plan_stats", "sdd_interface_mc_static", "sdd_plan_set_placement",
-                 "sdd_plan_placement", "sdd_mesh_quality"):
+                 "sdd_plan_placement", "sdd_mesh_quality", "sdd_mesh_smooth"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -256,7 +258,8 @@ def sdd_plan_edges(plan, n: int) -> np.ndarray:
 
 def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, chunk: int = 0,
               max_steps: int = 0, tie_delta: float = -1.0,
-              exit_test: int = SDD_EXIT_END_OF_STEP) -> sdd_mc_params:
+              exit_test: int = SDD_EXIT_END_OF_STEP,
+              stepper: int = SDD_STEP_EULER) -> sdd_mc_params:
     m = sdd_mc_params()
     m.paths_per_node = int(paths)
     m.dt = float(dt)
@@ -266,6 +269,7 @@ def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, c
     m.max_steps = int(max_steps)
     m.tie_delta = float(tie_delta)
     m.exit_test = int(exit_test)
+    m.stepper = int(stepper)
     return m
 
 
@@ -397,6 +401,12 @@ def sdd_mesh_quality(plan, mesh, ref=None, stream=None) -> dict:
     return {name: getattr(q, name) for name, _ in sdd_quality._fields_}
 
 
+def sdd_mesh_smooth(plan, mesh, steps: int, dt: float, k: float, stream=None) -> None:
+    """Perona-Malik smoothing of `mesh` [n][n][2] in place (host or device)."""
+    _check(load().sdd_mesh_smooth(plan, _ptr(mesh), int(steps), float(dt), float(k),
+                                  _stream(stream)), "sdd_mesh_smooth")
+
+
 def sdd_plan_destroy(plan) -> None:
     if plan:
         load().sdd_plan_destroy(plan)
@@ -437,7 +447,8 @@ class Plan:
         s = self.spec
         args = dict(paths=s.paths, dt=s.dt, seed=s.seed, precision=s.precision,
                     max_steps=s.max_steps, tie_delta=s.tie_delta,
-                    exit_test=getattr(s, "exit_test", SDD_EXIT_END_OF_STEP))
+                    exit_test=getattr(s, "exit_test", SDD_EXIT_END_OF_STEP),
+                    stepper=getattr(s, "stepper", SDD_STEP_EULER))
         args.update(kw)
         return mc_params(**args)
 

@@ -29,6 +29,7 @@ COEF_W, COEF_INV_W = 0, 1
 BMAP_IDENTITY, BMAP_PAPER_1D, BMAP_TABLE = 0, 1, 2
 FP64, FP32_STEP = 0, 1
 EXIT_END_OF_STEP, EXIT_BRIDGE = 0, 1
+STEP_EULER, STEP_EXPONENTIAL = 0, 1
 SOLVER_SOR, SOLVER_CG_FP32_REFINE = 0, 1
 
 
@@ -51,6 +52,7 @@ class MeshSpec:
     solver: int = SOLVER_SOR
     tol: float = 1e-10
     exit_test: int = EXIT_END_OF_STEP
+    stepper: int = STEP_EULER    # EXPONENTIAL: step lengths ~ Exp(1/dt), mean dt
     label: str = ""
 
     def cap(self) -> int:
