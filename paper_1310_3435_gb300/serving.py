@@ -26,7 +26,7 @@ import numpy as np
 
 from . import native as N
 
-SLOT_BYTES = 144            # device bytes of one work-item slot
+SLOT_BYTES = 152            # device bytes of one work-item slot
 
 
 @dataclass
