@@ -130,3 +130,19 @@ def test_unknown_stepper_is_rejected():
     with gpu_plan(spec) as P:
         with pytest.raises(N.SddError):
             N.sdd_interface_mc_sums(P.handle, P.mc_params(stepper=7))
+
+
+def test_exponential_edge_cases(orc):
+    """n = 3 (one node), N = 2, and a step cap of 3 that ends most paths:
+    counts and capped scores replay the oracle."""
+    for cap, et in ((3, W.EXIT_END_OF_STEP), (3, W.EXIT_BRIDGE), (0, W.EXIT_BRIDGE)):
+        spec = W.MeshSpec(n=3, sx=2, sy=2, family=W.FAMILY_RING,
+                          params=(10.0, 0.5, 0.5, 50.0, 0.25), paths=2, dt=1e-3, seed=7,
+                          max_steps=cap, stepper=W.STEP_EXPONENTIAL, exit_test=et)
+        nodes = orc.interface_nodes(spec.n, spec.sx, spec.sy)
+        g = gpu_sums(spec)
+        o = _oracle(orc, spec, nodes)
+        assert np.array_equal(g["paths"], o["paths"])
+        assert np.array_equal(g["non_exits"], o["non_exits"])
+        assert np.array_equal(g["steps"], o["steps"])
+        assert np.allclose(g["sum"], o["S_all"], rtol=1e-11, atol=1e-15)

@@ -110,3 +110,19 @@ def test_smoothing_improves_a_noisy_probabilistic_mesh(orc):
         q1 = N.sdd_mesh_quality(P.handle, sm, ref)
     assert q1["q_max"] < q0["q_max"] and q1["l_inf"] < q0["l_inf"]
     assert abs(q1["r_max"] - 1.0) < abs(q0["r_max"] - 1.0)
+
+
+def test_smoothing_and_fully_probabilistic_edge_cases(orc):
+    """n = 3: one interior node, one smoothing stencil; the fully
+    probabilistic plan has that one node."""
+    from paper_1310_3435_gb300 import native as N
+    spec = W.MeshSpec(n=3, sx=2, sy=2, family=W.FAMILY_BUMPS,
+                      params=W.bumps((4.0, 0.4, 0.6, 20.0, 20.0)), paths=64, dt=1e-3)
+    U = _noisy_mesh(3, seed=5, amp=0.05)
+    dt = 0.25 * 0.25                                  # h = 1/2: r = dt/h^2 = 1/4 exactly
+    want = orc.perona_malik(U, 3, dt, 0.7)
+    with gpu_plan(spec) as P:
+        assert P.n_nodes == 1
+        got = U.copy()
+        N.sdd_mesh_smooth(P.handle, got, 3, dt, 0.7)
+    assert np.max(np.abs(got - want)) < 1e-15
