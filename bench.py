@@ -65,6 +65,31 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# DRAM bytes (read + write) of one launch of the path kernel at the 257 x 257
+# ring workload with constant steps and the end-of-step test, from one ncu
+# capture of the timed launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# profiles/k_paths_fp32_ring257_launches.md).  Valid only for the kernel source
+# it was taken on: the bench line reports null traffic once the source's
+# SHA-256 differs.
+PATH_KERNEL_TRAFFIC = {"bytes": None, "source_sha256": None}
+
+
+def path_kernel_traffic(spec):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1310_3435_gb300", "csrc", "mc.cu")
+    try:
+        with open(src, "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    default = (spec.n, spec.sx, spec.family, spec.paths, spec.dt, spec.stepper,
+               spec.exit_test) == (257, 4, W.FAMILY_RING, 100000, 1e-5, W.STEP_EULER,
+                                   W.EXIT_END_OF_STEP)
+    if default and digest == PATH_KERNEL_TRAFFIC["source_sha256"]:
+        return PATH_KERNEL_TRAFFIC["bytes"]
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -343,7 +368,7 @@ def run_native(args):
         "max_stderr": float(mc_stats.max_stderr),
         "non_exits": int(mc_stats.non_exits),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak, "traffic": path_kernel_traffic(spec),
                      "kernel": "k_paths<FP32> (+k_reduce)",
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                                    % (sms, sm_clock_max, peak_kind),

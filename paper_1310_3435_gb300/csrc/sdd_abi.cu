@@ -13,9 +13,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sdd_internal.h"
 
 namespace sdd {
+
+// NVTX range around an ABI call (host timeline; a profiler filters kernels by
+// it, e.g. ncu --nvtx --nvtx-include "sdd_interface_mc/").
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- errors --
 namespace {
@@ -694,6 +705,7 @@ extern "C" {
 int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap* bmap,
                   sdd_plan** out)
 {
+    NvtxRange nvtx_range("sdd_mesh_plan");
     clear_error();
     if (!out) return fail(SDD_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -843,6 +855,7 @@ int sdd_plan_edges(const sdd_plan* plan, double* edges)
 int sdd_interface_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean, double* stderr_,
                      sdd_mc_stats* stats, void* stream_)
 {
+    NvtxRange nvtx_range("sdd_interface_mc");
     clear_error();
     if (!p) return fail(SDD_ERR_INVALID_ARG, "plan is NULL");
     int rc = check_device(p);
@@ -869,6 +882,7 @@ int sdd_interface_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean, double*
 int sdd_interface_mc_sums(sdd_plan* p, const sdd_mc_params* mc, sdd_node_sums* sums,
                           void* stream_)
 {
+    NvtxRange nvtx_range("sdd_interface_mc_sums");
     clear_error();
     if (!p || !sums) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     int rc = check_device(p);
@@ -904,6 +918,7 @@ int sdd_plan_last_mc_stats(sdd_plan* p, sdd_mc_stats* stats)
 int sdd_subdomain_solve(sdd_plan* p, const double* iface, const sdd_solve_params* sp, double* mesh,
                         sdd_solve_stats* stats, void* stream_)
 {
+    NvtxRange nvtx_range("sdd_subdomain_solve");
     clear_error();
     if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     if (!iface && p->n_nodes > 0) return fail(SDD_ERR_INVALID_ARG, "iface is NULL");
@@ -933,6 +948,7 @@ int sdd_mesh_generate(sdd_plan* p, const sdd_mc_params* mc, const sdd_solve_para
                       double* mesh, double* iface_mean, double* iface_stderr,
                       sdd_mc_stats* mc_stats, sdd_solve_stats* solve_stats, void* stream_)
 {
+    NvtxRange nvtx_range("sdd_mesh_generate");
     clear_error();
     if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     int rc = check_device(p);
@@ -1073,6 +1089,7 @@ int sdd_plan_placement(const sdd_plan* p, uint8_t* mask, int64_t* n_mc)
 int sdd_mesh_quality(sdd_plan* p, const double* mesh, const double* ref, sdd_quality* out,
                      void* stream_)
 {
+    NvtxRange nvtx_range("sdd_mesh_quality");
     clear_error();
     if (!p || !mesh || !out) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     int rc = check_device(p);
@@ -1123,6 +1140,7 @@ int sdd_mesh_quality(sdd_plan* p, const double* mesh, const double* ref, sdd_qua
 
 int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, void* stream_)
 {
+    NvtxRange nvtx_range("sdd_mesh_smooth");
     clear_error();
     if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     if (steps < 0) return fail(SDD_ERR_INVALID_ARG, "steps must be >= 0");
@@ -1164,6 +1182,7 @@ int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, v
 int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* mc,
                      const sdd_solve_params* sp, sdd_batch** out)
 {
+    NvtxRange nvtx_range("sdd_batch_create");
     clear_error();
     if (!out) return fail(SDD_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -1370,6 +1389,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
 
 int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
 {
+    NvtxRange nvtx_range("sdd_batch_run");
     clear_error();
     if (!b) return fail(SDD_ERR_INVALID_ARG, "batch is NULL");
     int dev = -1;
@@ -1418,6 +1438,7 @@ int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
 
 int sdd_batch_run_phases(sdd_batch* b, int phases, void* stream_)
 {
+    NvtxRange nvtx_range("sdd_batch_run_phases");
     clear_error();
     if (!b) return fail(SDD_ERR_INVALID_ARG, "batch is NULL");
     if (phases < 1 || phases > 3) return fail(SDD_ERR_INVALID_ARG, "phases must be 1, 2 or 3");

@@ -201,3 +201,29 @@ def test_fp32_bridge_paired_with_fp64(orc):
     m32, _ = gpu_means(g32, spec.n, nodes)
     assert np.all(np.abs(m32 - m64) <= se64)
     assert abs(int(g32["steps"].sum()) - int(g64["steps"].sum())) / g64["steps"].sum() < 2e-3
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.FP32_STEP])
+def test_outputs_stay_inside_their_buffers(precision):
+    """Canary rows after every device output (means, std-errs, node sums,
+    mesh, smoothed mesh) are untouched: no kernel writes past its rows."""
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    spec = W.small_parity_cases()[1]
+    pad = 7
+    with gpu_plan(spec) as P:
+        m = P.n_nodes
+        mean = torch.full((m + pad, 2), float("nan"), dtype=torch.float64, device="cuda")
+        se = torch.full((m + pad, 2), float("nan"), dtype=torch.float64, device="cuda")
+        N.sdd_interface_mc(P.handle, P.mc_params(precision=precision), mean[:m], se[:m])
+        sums = torch.full((m + pad, 12), -7, dtype=torch.int64, device="cuda")
+        N.sdd_interface_mc_sums(P.handle, P.mc_params(precision=precision), sums[:m])
+        n = spec.n
+        mesh = torch.full((n * n * 2 + pad,), float("nan"), dtype=torch.float64, device="cuda")
+        N.sdd_subdomain_solve(P.handle, mean[:m], P.solve_params(), mesh[:n * n * 2])
+        N.sdd_mesh_smooth(P.handle, mesh[:n * n * 2], 3, 0.2 / (n - 1) ** 2, 1.0)
+        torch.cuda.synchronize()
+        assert torch.isfinite(mean[:m]).all() and torch.isfinite(se[:m]).all()
+        assert torch.isnan(mean[m:]).all() and torch.isnan(se[m:]).all()
+        assert (sums[m:] == -7).all()
+        assert torch.isfinite(mesh[:n * n * 2]).all() and torch.isnan(mesh[n * n * 2:]).all()
