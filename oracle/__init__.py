@@ -305,11 +305,11 @@ def path(n: int, s0: float, t0: float, node: int, path_index: int, edges: np.nda
     return {"F": F, "steps": int(st.value), "tie": bool(tie.value), "capped": bool(cap.value)}
 
 
-def step_lengths(seed: int, node: int, path: int, step_pair: int) -> np.ndarray:
-    """Unit-mean exponentials of the lengths of steps 2 step_pair and
-    2 step_pair + 1 under exponential time stepping (§2.2)."""
-    E = np.zeros(2, dtype=np.float64)
-    lib().oracle_step_lengths(seed, node, path, step_pair, _dp(E))
+def step_lengths(seed: int, node: int, path: int, quad: int) -> np.ndarray:
+    """Unit-mean exponentials of the lengths of steps 4 quad .. 4 quad + 3
+    under exponential time stepping (§2.2)."""
+    E = np.zeros(4, dtype=np.float64)
+    lib().oracle_step_lengths(seed, node, path, quad, _dp(E))
     return E
 
 

@@ -33,9 +33,9 @@
  *
  * Exponential time stepping (§2.2, after Jansons and Lythe): step k has the
  * random length h_k = dt E_k, E_k = -ln U a unit-mean exponential, so the
- * steps have the density lambda exp(-lambda h) with lambda = 1/dt.  The two
- * lengths of steps k and k+1 (k even) come from words 0 and 1 of
- * Philox(counter = (k/2, path, node, 2)).  Given h_k the update is the
+ * steps have the density lambda exp(-lambda h) with lambda = 1/dt.  The four
+ * lengths of steps 4m .. 4m+3 come from words 0..3 of
+ * Philox(counter = (m, path, node, 2)).  Given h_k the update is the
  * Euler-Maruyama one with step h_k, and the boundary test is the exact
  * crossing probability of the step's Brownian bridge over the time h_k (the
  * Brownian-bridge test below with dt replaced by h_k), which is how the
@@ -100,17 +100,17 @@ void oracle_normals(uint64_t seed, uint32_t node, uint32_t path, uint32_t step_p
     z[3] = rb * sin(2.0 * M_PI * u[3]);
 }
 
-/* Unit-mean exponentials E_k, E_k+1 of the step lengths of steps k and k+1
- * (k even) under exponential time stepping: E = -ln U, U = (r + 1/2) 2^-32
- * from words 0 and 1 of Philox(counter = (k/2, path, node, 2)). */
-void oracle_step_lengths(uint64_t seed, uint32_t node, uint32_t path, uint32_t step_pair,
-                         double E[2])
+/* Unit-mean exponentials of the lengths of steps 4q .. 4q+3 under exponential
+ * time stepping: E = -ln U, U = (r + 1/2) 2^-32 from words 0..3 of
+ * Philox(counter = (q, path, node, 2)). */
+void oracle_step_lengths(uint64_t seed, uint32_t node, uint32_t path, uint32_t quad,
+                         double E[4])
 {
-    uint32_t ctr[4] = {step_pair, path, node, 2u};
+    uint32_t ctr[4] = {quad, path, node, 2u};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t r[4];
     oracle_philox4x32_10(ctr, key, r);
-    for (int m = 0; m < 2; ++m)
+    for (int m = 0; m < 4; ++m)
         E[m] = -log(((double)r[m] + 0.5) * 0x1p-32);
 }
 
@@ -318,19 +318,18 @@ void oracle_path(int n, double s0, double t0, uint32_t node, uint32_t path,
 {
     double xs = s0, xt = t0;
     double z[4];
-    double E[2] = {1.0, 1.0};
+    double E[4] = {1.0, 1.0, 1.0, 1.0};
     int flag = 0;
     uint64_t k = 0;
     double e[2];
     int edge = -1;
     while (k < max_steps) {
-        if ((k & 1u) == 0) {
+        if ((k & 1u) == 0)
             oracle_normals(seed, node, path, (uint32_t)(k >> 1), z);
-            if (stepper == 1)
-                oracle_step_lengths(seed, node, path, (uint32_t)(k >> 1), E);
-        }
+        if (stepper == 1 && (k & 3u) == 0)
+            oracle_step_lengths(seed, node, path, (uint32_t)(k >> 2), E);
         const double* zk = z + 2 * (int)(k & 1u);
-        double h = stepper == 1 ? dt * E[k & 1u] : dt;
+        double h = stepper == 1 ? dt * E[k & 3u] : dt;
         double sq = sqrt(2.0 * h);
         double b[2];
         oracle_drift(family, coef_mode, p, xs, xt, b);

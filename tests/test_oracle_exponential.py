@@ -23,13 +23,14 @@ FLAT = (0.0,)                     # c = 1: no drift
 def test_step_lengths_are_unit_exponentials(orc):
     from scipy import stats
     E = np.array([orc.step_lengths(7, 3, q, k) for q in range(4000) for k in range(5)])
-    assert E.min() > 0.0
-    for col in range(2):
+    assert E.shape[1] == 4 and E.min() > 0.0
+    for col in range(4):
         assert stats.kstest(E[:, col], "expon").pvalue > 1e-3
     assert abs(E.mean() - 1.0) < 4.0 / math.sqrt(E.size)
-    # the two words of a block are independent, and independent of the
-    # normals drawn from the same counter (a different stream word)
-    assert abs(np.corrcoef(E[:, 0], E[:, 1])[0, 1]) < 4.0 / math.sqrt(len(E))
+    # the words of a block are independent of each other, and of the normals
+    # drawn from the same counter (a different stream word)
+    for a, b in ((0, 1), (1, 2), (2, 3), (0, 3)):
+        assert abs(np.corrcoef(E[:, a], E[:, b])[0, 1]) < 4.0 / math.sqrt(len(E))
     Z = np.array([orc.normals(7, 3, q, k) for q in range(4000) for k in range(5)])
     assert abs(np.corrcoef(E[:, 0], Z[:, 0] ** 2)[0, 1]) < 4.0 / math.sqrt(len(E))
 
