@@ -39,10 +39,10 @@ import workloads as W  # noqa: E402
 #   two uniforms (shift-or + add): 4;  Box-Muller pair: 10;  ring drift: 22;
 #   Euler-Maruyama update: 4;  exit test: 6;  step count and cap test: 2
 OPS_PER_STEP_RING_FP32 = 30 + 4 + 10 + 22 + 4 + 6 + 2        # = 78
-# Exponential time stepping adds per step: half a Philox block for the two
-# step lengths (30), one uniform (2), -log2 U with its clamp and the scale by
-# ln 2 (3), the length into the noise scale (1) and into the drift (1).
-OPS_EXPO_EXTRA = 30 + 2 + 3 + 1 + 1                           # = 37
+# Exponential time stepping adds per step: a quarter of a Philox block for
+# the step lengths (15), one uniform (2), -log2 U with its clamp and the scale
+# by ln 2 (3), the length into the noise scale (1) and into the drift (1).
+OPS_EXPO_EXTRA = 15 + 2 + 3 + 1 + 1                           # = 22
 # The Brownian-bridge test adds the distance test of a step pair's three
 # points (9 per pair); with exponential steps also the pair's largest length
 # into sqrt(23 h) (3 per pair).

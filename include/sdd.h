@@ -104,8 +104,8 @@ extern "C" {
  *   EXPONENTIAL : exponential time stepping (after Jansons and Lythe): step k
  *                 has the random length h = dt E, E = -ln U a unit-mean
  *                 exponential (density lambda exp(-lambda h), lambda = 1/dt),
- *                 U from words 0 and 1 of Philox counter (k/2, path, node, 2)
- *                 for steps k, k+1 (k even); the update is the Euler-Maruyama
+ *                 U from word k mod 4 of Philox counter (k/4, path, node, 2);
+ *                 the update is the Euler-Maruyama
  *                 one with step h, and the Brownian-bridge test (with
  *                 SDD_EXIT_BRIDGE) uses h in place of dt.  dt is the mean
  *                 step 1/lambda; the default step cap stays ceil(2/dt). */

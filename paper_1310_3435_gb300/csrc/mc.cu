@@ -137,9 +137,9 @@ __device__ __forceinline__ void box_muller_f32_step(uint32_t ra, uint32_t rb, fl
     sz = sin_approx(ang);
 }
 
-// Exponential time stepping (§2.2): the lengths of steps k, k+1 (k even) are
-// dt E with E = -ln U, U from words 0 and 1 of Philox counter
-// (k/2, path, node, 2).  FP64: U = (r + 1/2) 2^-32.  FP32: returns
+// Exponential time stepping (§2.2): the lengths of steps 4q .. 4q+3 are dt E
+// with E = -ln U, U from words 0..3 of Philox counter (q, path, node, 2).
+// FP64: U = (r + 1/2) 2^-32.  FP32: returns
 // E / ln 2 = -log2 U with the FP32 uniform, clamped at 0 (the approximate
 // log2 of a U next to 1 may land on the wrong side of 0).
 __device__ __forceinline__ double exp_unit_f64(uint32_t r)
@@ -552,6 +552,7 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
 
     const bool bridge = M.bridge != 0;
     const bool expo = M.stepper == SDD_STEP_EXPONENTIAL;
+    uint4 Lq = make_uint4(0u, 0u, 0u, 0u);     // Philox block of the current four step lengths
     const R inv_dt = R(1) / dtR, qmax = R(23) * dtR;
     int bedge = -1;
     R btau = R(0);
@@ -596,13 +597,16 @@ __device__ __forceinline__ void run_item(const MeshDev& M, const Dens& dens, con
             }
             R h0 = dtR, h1 = dtR;
             if (expo) {
-                const uint4 L = philox(make_uint4(k >> 1, path, nid, 2u));
+                // lengths of steps 4q..4q+3 from one block: words x, y for the
+                // first pair of the four steps, z, w for the second
+                if ((k & 2u) == 0u) Lq = philox(make_uint4(k >> 2, path, nid, 2u));
+                const uint32_t wa = (k & 2u) ? Lq.z : Lq.x, wb = (k & 2u) ? Lq.w : Lq.y;
                 if constexpr (PREC == SDD_FP64) {
-                    h0 = dtR * exp_unit_f64(L.x);
-                    h1 = dtR * exp_unit_f64(L.y);
+                    h0 = dtR * exp_unit_f64(wa);
+                    h1 = dtR * exp_unit_f64(wb);
                 } else {
-                    h0 = dtR * (exp_unit_log2_f32(L.x) * 0.69314718055994530942f);
-                    h1 = dtR * (exp_unit_log2_f32(L.y) * 0.69314718055994530942f);
+                    h0 = dtR * (exp_unit_log2_f32(wa) * 0.69314718055994530942f);
+                    h1 = dtR * (exp_unit_log2_f32(wb) * 0.69314718055994530942f);
                 }
             }
             if (k + 2u <= kmax) {
@@ -882,11 +886,16 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
 
     // `need` is warp-uniform: the refill runs once at the start and then only
     // after some path ended (only an ended path can free a lane, close a set or
-    // change what can be handed out).
+    // change what can be handed out).  With exponential steps paths start only
+    // on even pair iterations `it`, so every lane of the warp is at the same
+    // place in its four-step block of lengths: the block's Philox call is
+    // warp-uniform, once per two pairs (an ended lane may idle for a pair).
     unsigned dm = 0u;
     bool need = true;
+    uint32_t it = 0;
+    uint32_t hz = 0u, hw = 0u;                 // words z, w of the current length block
     for (int guard = 0;;) {
-        if (need) {
+        if (need && (!EXPO || (it & 1u) == 0u)) {
             need = false;
             const unsigned idle = __ballot_sync(FULL, !active);
             const Refill rf = stream_refill(M, a, W, lane, dm, idle, mesh_end);
@@ -928,9 +937,16 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
             // steps are exponential)
             float fa = 1.0f, fb = 1.0f;
             if constexpr (EXPO) {
-                const uint4 L = philox(make_uint4(k >> 1, path, nid, 2u));
-                fa = exp_unit_log2_f32(L.x) * LN2F;
-                fb = exp_unit_log2_f32(L.y) * LN2F;
+                uint32_t wa = hz, wb = hw;
+                if ((it & 1u) == 0u) {                 // k = 4q: a new block of four lengths
+                    const uint4 L = philox(make_uint4(k >> 2, path, nid, 2u));
+                    wa = L.x;
+                    wb = L.y;
+                    hz = L.z;
+                    hw = L.w;
+                }
+                fa = exp_unit_log2_f32(wa) * LN2F;
+                fb = exp_unit_log2_f32(wb) * LN2F;
             }
             float na, ca, sa, nb, cb, sb;
             box_muller_f32_step(r.x, r.y, c4dt * fa, na, ca, sa);
@@ -1008,8 +1024,9 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                 (void)ps; (void)pt;
             }
         }
-        dm = __ballot_sync(FULL, ended);
+        dm |= __ballot_sync(FULL, ended);          // kept until the next refill
         need = dm != 0u;
+        ++it;
     }
 }
 
