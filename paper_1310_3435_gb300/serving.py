@@ -14,6 +14,12 @@ released stream-ordered, and the memory budget is handed back.
 Every request keeps its own Philox key and work-item size, so its result is
 bitwise the same alone and in any mix (see tests/test_gpu_serving.py).
 PyTorch is used for streams, events and pinned host buffers only.
+
+Failures stay with the requests they hit: a request whose plan or pilot
+cannot be built, or every request of a batch that cannot be launched, is
+answered with status "failed" and the error, its memory is given back, and
+the server carries on.  `cancel(rid)` drops a request that has not reached a
+batch, or discards the results of one whose batch is running.
 """
 from __future__ import annotations
 
@@ -51,6 +57,8 @@ class Result:
     started: float
     done: float
     batch: int
+    status: str = "ok"           # "ok", "failed" (error holds why) or "cancelled"
+    error: str = ""
 
     @property
     def latency(self) -> float:
@@ -123,6 +131,18 @@ class Server:
         self.used = 0
         self.peak_used = 0
         self.launches = 0
+        self._cancel = set()
+
+    def cancel(self, rid: int) -> None:
+        """Cancels request `rid`: a request not yet in a batch is dropped at
+        the next turn of the loop; one whose batch is running is reported as
+        cancelled (without results) when the batch completes."""
+        self._cancel.add(rid)
+
+    @staticmethod
+    def _dropped(req, status, error, t, batch=-1):
+        return Result(req.rid, req.spec, 0, None, None, None, 0, math.nan, req.arrival, t, t, t,
+                      batch, status=status, error=error)
 
     def _paths_for(self, spec, pilot_stats) -> int:
         """N = ceil((sigma_max / target)^2) with sigma = pilot stderr sqrt(N_pilot)."""
@@ -158,27 +178,60 @@ class Server:
                 if self.used + base > self.budget and (piloting or ready or inflight):
                     break                                   # wait for memory to free up
                 pending.popleft()
-                plan = N.Plan(req.spec)
+                progressed = True
+                if req.rid in self._cancel:
+                    results.append(self._dropped(req, "cancelled", "", now()))
+                    continue
+                try:
+                    plan = N.Plan(req.spec)
+                except Exception as e:                  # malformed request, no memory, ...
+                    results.append(self._dropped(req, "failed", str(e), now()))
+                    continue
                 self.used += base
                 self.peak_used = max(self.peak_used, self.used)
                 ev = None
                 if self.target:
-                    N.sdd_interface_mc(plan.handle, plan.mc_params(paths=self.pilot_paths),
-                                       want_stats=False, stream=self.pilot_stream)
+                    try:
+                        N.sdd_interface_mc(plan.handle, plan.mc_params(paths=self.pilot_paths),
+                                           want_stats=False, stream=self.pilot_stream)
+                    except Exception as e:
+                        plan.close()
+                        self.used -= base
+                        results.append(self._dropped(req, "failed", str(e), now()))
+                        continue
                     ev = cuda.Event()
                     ev.record(self.pilot_stream)
                 piloting.append([req, plan, ev, base, now()])
-                progressed = True
             # 2. pilots done -> paths per node chosen, memory re-estimated
             while piloting and (piloting[0][2] is None or piloting[0][2].query()):
                 req, plan, ev, base, ta = piloting.popleft()
-                st = N.sdd_plan_last_mc_stats(plan.handle) if ev is not None else None
-                paths = self._paths_for(req.spec, st)
+                progressed = True
+                try:
+                    st = N.sdd_plan_last_mc_stats(plan.handle) if ev is not None else None
+                    paths = self._paths_for(req.spec, st)
+                except Exception as e:
+                    plan.close()
+                    self.used -= base
+                    results.append(self._dropped(req, "failed", str(e), now()))
+                    continue
                 nbytes = device_bytes(req.spec.n, plan.n_nodes, paths, self.sms)
                 self.used += nbytes - base
                 self.peak_used = max(self.peak_used, self.used)
                 ready.append([req, plan, paths, nbytes, ta])
-                progressed = True
+            # cancelled requests leave the queues before they reach a batch
+            if self._cancel:
+                for q in (piloting, ready):
+                    keep = deque()
+                    for x in q:
+                        if x[0].rid in self._cancel:
+                            x[1].close()
+                            self.used -= x[3]
+                            results.append(self._dropped(x[0], "cancelled", "", now()))
+                            progressed = True
+                        else:
+                            keep.append(x)
+                    q.clear()
+                    q.extend(keep)
             # 3. launch the ready requests as one batch on a free stream: at once
             # when the device is idle; while a batch runs, let the ready queue
             # fill up (to max_batch, or until its oldest request has waited
@@ -189,11 +242,24 @@ class Server:
                 take = [ready.popleft() for _ in range(min(self.max_batch, len(ready)))]
                 plans = [x[1] for x in take]
                 mcs = [p.mc_params(paths=x[2]) for p, x in zip(plans, take)]
-                batch = N.Batch(plans, mcs, [p.solve_params() for p in plans])
                 si = free_streams.popleft()
                 stream = self.streams[si]
                 started = now()
-                batch.run(use_graph=self.use_graph, stream=stream)
+                batch = None
+                try:
+                    batch = N.Batch(plans, mcs, [p.solve_params() for p in plans])
+                    batch.run(use_graph=self.use_graph, stream=stream)
+                except Exception as e:                  # the whole batch fails
+                    if batch is not None:
+                        batch.close()
+                    for x in take:
+                        x[1].close()
+                        self.used -= x[3]
+                        results.append(self._dropped(x[0], "failed", str(e), now(), bid))
+                    free_streams.append(si)
+                    bid += 1
+                    progressed = True
+                    continue
                 ev = cuda.Event()
                 ev.record(stream)
                 inflight.append(_InFlight(bid, batch, [x[0] for x in take], plans,
@@ -210,16 +276,27 @@ class Server:
                 if f.event.query():
                     done = now()
                     for k, (req, plan) in enumerate(zip(f.reqs, f.plans)):
+                        admitted = getattr(req, "admitted_at", f.started)
+                        if req.rid in self._cancel:
+                            results.append(Result(req.rid, req.spec, f.paths[k], None, None, None,
+                                                  0, math.nan, req.arrival, admitted, f.started,
+                                                  done, f.bid, status="cancelled"))
+                            continue
                         n = plan.n
                         mesh = np.empty((n, n, 2))
                         mean = np.empty((plan.n_nodes, 2))
                         se = np.empty((plan.n_nodes, 2))
-                        N.sdd_plan_results(plan.handle, mesh, mean, se, stream=f.stream[1])
-                        ms, _ = f.batch.stats(k, allow_not_converged=True)
+                        try:
+                            N.sdd_plan_results(plan.handle, mesh, mean, se, stream=f.stream[1])
+                            ms, _ = f.batch.stats(k, allow_not_converged=True)
+                        except Exception as e:
+                            results.append(Result(req.rid, req.spec, f.paths[k], None, None, None,
+                                                  0, math.nan, req.arrival, admitted, f.started,
+                                                  done, f.bid, status="failed", error=str(e)))
+                            continue
                         results.append(Result(req.rid, req.spec, f.paths[k], mesh, mean, se,
                                               int(ms.path_steps), float(ms.max_stderr),
-                                              req.arrival, getattr(req, "admitted_at", f.started),
-                                              f.started, done, f.bid))
+                                              req.arrival, admitted, f.started, done, f.bid))
                     f.batch.close()
                     for plan in f.plans:
                         plan.close()
@@ -240,9 +317,13 @@ class Server:
 
 
 def summarize(results, wall: float | None = None) -> dict:
-    """p50 / p99 latency, meshes/s and path-steps/s of a served run."""
+    """p50 / p99 latency, meshes/s and path-steps/s of a served run (over the
+    requests served; failed and cancelled ones are counted apart)."""
+    failed = sum(1 for r in results if r.status == "failed")
+    cancelled = sum(1 for r in results if r.status == "cancelled")
+    results = [r for r in results if r.status == "ok"]
     if not results:
-        return {"requests": 0}
+        return {"requests": 0, "failed": failed, "cancelled": cancelled}
     lat = np.array([r.latency for r in results])
     t_first = min(r.arrival for r in results)
     t_last = max(r.done for r in results)
@@ -252,4 +333,5 @@ def summarize(results, wall: float | None = None) -> dict:
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
             "meshes_per_s": len(results) / span, "path_steps_per_s": steps / span,
             "span_s": span, "max_stderr": float(max(r.max_stderr for r in results)),
-            "batches": len({r.batch for r in results})}
+            "batches": len({r.batch for r in results}), "failed": failed,
+            "cancelled": cancelled}

@@ -53,3 +53,42 @@ def test_two_ranks_share_nothing_but_the_timing():
     assert set(m0).isdisjoint(m1) and sorted(m0 + m1) == list(range(10))
     assert t0 == t1 == 2.0
     assert v0 == v1 == 100.0 * 2 / 2.0
+
+
+def _dying_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import datetime
+    import torch.distributed as dist
+    from paper_1310_3435_gb300 import replicas as R
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)                         # the rank dies between steps
+    try:
+        R.max_over_ranks(1.0)
+        q.put((rank, "no error"))
+    except Exception as e:                  # the survivor learns of it, no hang
+        q.put((rank, type(e).__name__))
+
+
+def test_a_dead_rank_is_detected_by_the_timing_collective():
+    """Failure detection on the host: rank 1 exits before the max-over-ranks
+    collective; rank 0's collective ends with an error within the process
+    group's timeout instead of waiting for ever."""
+    import time
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dying_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    rank, what = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and what != "no error", what
+    assert procs[1].exitcode == 3
+    assert time.time() - t0 < 100

@@ -159,3 +159,66 @@ def test_batches_overlap_on_streams_and_latency_includes_queueing():
     # with two streams, some batch starts before an earlier one is done
     assert any(b[0] < a[1] for a, b in zip(starts, starts[1:]) if b[0] > a[0])
     assert all(r.done >= r.started >= r.arrival for r in res)
+
+
+class FaultyLib(FakeLib):
+    """Failures injected on the host: the plan of request `bad_plan` cannot be
+    built (a malformed or oversized request), and every batch holding request
+    `bad_batch` fails to launch."""
+
+    def __init__(self, bad_plan, bad_batch):
+        super().__init__()
+        self.bad_plan, self.bad_batch = bad_plan, bad_batch
+
+    def Plan(self, spec):
+        if spec.label == "req%d" % self.bad_plan:
+            raise RuntimeError("injected: plan allocation failed")
+        return FakeLib._Plan(self, spec)
+
+    def Batch(self, plans, mcs, sps):
+        if any(p.spec.label == "req%d" % self.bad_batch for p in plans):
+            raise RuntimeError("injected: batch launch failed")
+        return FakeLib._Batch(self, plans, mcs, sps)
+
+
+def test_failures_are_reported_and_the_server_carries_on():
+    lib = FaultyLib(bad_plan=3, bad_batch=11)
+    srv = S.Server(hbm_budget=1e12, n_streams=2, max_batch=4, target_stderr=1e-3,
+                   pilot_paths=1024, backend=lib, cuda=FakeCuda, sms=152)
+    res = srv.run(_requests(24, rate=3000.0))
+    by = {r.rid: r for r in res}
+    assert sorted(by) == list(range(24))              # every request gets an answer
+    assert by[3].status == "failed" and "plan allocation" in by[3].error
+    failed_batch = [r for r in res if r.status == "failed" and "batch launch" in r.error]
+    assert 11 in {r.rid for r in failed_batch}        # its batch mates fail with it
+    ok = [r for r in res if r.status == "ok"]
+    assert len(ok) == 24 - 1 - len(failed_batch) and all(r.mesh is not None for r in ok)
+    assert srv.used == 0 and lib.live_plans == 0      # memory and plans given back
+    s = S.summarize(res)
+    assert s["requests"] == len(ok) and s["failed"] == 1 + len(failed_batch)
+
+
+def test_cancelled_requests():
+    lib = FakeLib()
+    reqs = _requests(16, rate=4000.0)
+    srv = S.Server(hbm_budget=1e12, n_streams=1, max_batch=4, target_stderr=None,
+                   backend=lib, cuda=FakeCuda, sms=152)
+    srv.cancel(5)                                      # cancelled before it arrives
+    last = reqs[-1].rid
+    orig_run = FakeLib._Batch.run
+
+    def run_and_cancel(self, use_graph=False, stream=None):
+        orig_run(self, use_graph, stream)
+        if any(p.spec.label == "req%d" % last for p in self.plans):
+            srv.cancel(last)                           # cancelled while its batch runs
+    FakeLib._Batch.run = run_and_cancel
+    try:
+        res = srv.run(reqs)
+    finally:
+        FakeLib._Batch.run = orig_run
+    by = {r.rid: r for r in res}
+    assert sorted(by) == list(range(16))
+    assert by[5].status == "cancelled" and by[5].mesh is None
+    assert by[last].status == "cancelled" and by[last].mesh is None
+    assert all(r.status == "ok" for k, r in by.items() if k not in (5, last))
+    assert srv.used == 0 and lib.live_plans == 0
