@@ -71,7 +71,8 @@ def env_rank():
 # profiles/k_paths_fp32_ring257_launches.md).  Valid only for the kernel source
 # it was taken on: the bench line reports null traffic once the source's
 # SHA-256 differs.
-PATH_KERNEL_TRAFFIC = {"bytes": None, "source_sha256": None}
+PATH_KERNEL_TRAFFIC = {"bytes": 691460 + 118780,
+                       "source_sha256": "555c412d53233f3639b42305d9a939b6d311a4c60ef3cbea6bf890fde78fde58"}
 
 
 def path_kernel_traffic(spec):
@@ -369,6 +370,8 @@ def run_native(args):
         "non_exits": int(mc_stats.non_exits),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
                      "frac": achieved / alu_peak, "traffic": path_kernel_traffic(spec),
+                     "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                      "launch (ncu), bytes; null if the kernel source changed",
                      "kernel": "k_paths<FP32> (+k_reduce)",
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                                    % (sms, sm_clock_max, peak_kind),
