@@ -38,7 +38,7 @@ import numpy as np
 
 from . import build as _build
 
-FAMILY_BUMPS, FAMILY_RING, FAMILY_RIDGE = 0, 1, 2
+FAMILY_BUMPS, FAMILY_RING, FAMILY_RIDGE, FAMILY_TABLE = 0, 1, 2, 3
 COEF_W, COEF_INV_W = 0, 1
 BMAP_IDENTITY, BMAP_PAPER_1D, BMAP_TABLE = 0, 1, 2
 EDGE_BOTTOM, EDGE_TOP, EDGE_LEFT, EDGE_RIGHT = 0, 1, 2, 3
@@ -102,8 +102,10 @@ def _dp(a: np.ndarray):
 
 
 def _params(params) -> np.ndarray:
-    p = np.zeros(32, dtype=np.float64)
+    """Family parameters as a C array (at least 32 entries; a TABLE density
+    carries [tn, tn*tn values of ln w])."""
     q = np.asarray(params, dtype=np.float64).ravel()
+    p = np.zeros(max(32, q.size), dtype=np.float64)
     p[: q.size] = q
     return p
 
@@ -429,9 +431,17 @@ def closed_form_1d(family: int, coef_mode: int, params, x: np.ndarray, axis: int
         s, t = (y, other) if axis == 0 else (other, y)
         return 1.0 / float(coef(family, coef_mode, params, s, t))
 
-    total = quad(inv_c, 0.0, 1.0, limit=400, epsabs=1e-14, epsrel=1e-13)[0]
-    return np.array([quad(inv_c, 0.0, float(v), limit=400, epsabs=1e-14,
-                          epsrel=1e-13)[0] / total for v in np.atleast_1d(x)])
+    # a tabulated density is smooth inside its cells only: integrate cell by cell
+    tn = int(np.asarray(params, dtype=np.float64).ravel()[0]) if family == FAMILY_TABLE else 2
+    edges = np.arange(tn) / (tn - 1.0)
+
+    def integral(v):
+        cuts = [0.0] + [e for e in edges[1:-1] if e < v] + [v]
+        return sum(quad(inv_c, a, b, limit=400, epsabs=1e-15, epsrel=1e-13)[0]
+                   for a, b in zip(cuts[:-1], cuts[1:]) if b > a)
+
+    total = integral(1.0)
+    return np.array([integral(float(v)) / total for v in np.atleast_1d(x)])
 
 
 def torsion_exit_time(s: float, t: float, terms: int = 401) -> float:

@@ -124,13 +124,44 @@ void oracle_step_lengths(uint64_t seed, uint32_t node, uint32_t path, uint32_t q
  *             w = 1 + A sech^2(k (r - r0)),  r = |(s,t) - (cs,ct)|
  *   2 RIDGE : params = [A, k, t0, a, f]
  *             w = 1 + A exp(-k (t - t0 - a sin(2 pi f s))^2)
+ *   3 TABLE : params = [tn, L(0,0), L(1,0), ..., L(tn-1,tn-1)]: ln w at the
+ *             tn x tn nodes (a/(tn-1), b/(tn-1)), row b after row b-1;
+ *             w = exp(L), L the bilinear interpolant of the nodes, and
+ *             grad ln w = grad L, the interpolant's exact (cellwise) gradient
  * The generator's coefficient is c = w (coef_mode 0) or c = 1/w (coef_mode 1). */
+
+/* Bilinear interpolant L of a table of ln w and its gradient at (s,t); the
+ * cell is the one holding (s,t), the last one on the upper sides. */
+static void table_L(const double* p, double s, double t, double* L, double* Ls, double* Lt)
+{
+    int tn = (int)p[0];
+    const double* T = p + 1;
+    double m = (double)(tn - 1);
+    double x = s * m, y = t * m;
+    int a = (int)floor(x), b = (int)floor(y);
+    if (a > tn - 2) a = tn - 2;
+    if (a < 0) a = 0;
+    if (b > tn - 2) b = tn - 2;
+    if (b < 0) b = 0;
+    double fa = x - (double)a, fb = y - (double)b;
+    double L00 = T[b * tn + a], L10 = T[b * tn + a + 1];
+    double L01 = T[(b + 1) * tn + a], L11 = T[(b + 1) * tn + a + 1];
+    *L = (1.0 - fb) * ((1.0 - fa) * L00 + fa * L10) + fb * ((1.0 - fa) * L01 + fa * L11);
+    *Ls = ((1.0 - fb) * (L10 - L00) + fb * (L11 - L01)) * m;
+    *Lt = ((1.0 - fa) * (L01 - L00) + fa * (L11 - L10)) * m;
+}
 
 /* w and grad w at (s,t). */
 static void density_w(int family, const double* p, double s, double t,
                       double* w, double* ws, double* wt)
 {
-    if (family == 0) {
+    if (family == 3) {
+        double L, Ls, Lt;
+        table_L(p, s, t, &L, &Ls, &Lt);
+        *w = exp(L);
+        *ws = *w * Ls;
+        *wt = *w * Lt;
+    } else if (family == 0) {
         int nb = (int)p[0];
         double acc = 1.0, gs = 0.0, gt = 0.0;
         for (int b = 0; b < nb; ++b) {
@@ -183,6 +214,13 @@ void oracle_drift(int family, int coef_mode, const double* p, double s, double t
     double w, ws, wt;
     density_w(family, p, s, t, &w, &ws, &wt);
     double sign = coef_mode == 0 ? 1.0 : -1.0;
+    if (family == 3) {                       /* grad ln w = grad L directly */
+        double L, Ls, Lt;
+        table_L(p, s, t, &L, &Ls, &Lt);
+        b[0] = sign * Ls;
+        b[1] = sign * Lt;
+        return;
+    }
     b[0] = sign * ws / w;
     b[1] = sign * wt / w;
 }

@@ -16,6 +16,7 @@ Family parameter layouts (shared convention of both implementations):
   BUMPS (0): [nb, (A, cs, ct, ks, kt) * nb]   w = 1 + sum A exp(-ks(s-cs)^2 - kt(t-ct)^2)
   RING  (1): [A, cs, ct, k, r0]                w = 1 + A sech^2(k(|x-c| - r0))
   RIDGE (2): [A, k, t0, a, f]                  w = 1 + A exp(-k(t - t0 - a sin(2 pi f s))^2)
+  TABLE (3): [tn, tn*tn values of ln w at the nodes (a/(tn-1), b/(tn-1)), row by row in b]
 """
 from __future__ import annotations
 
@@ -24,7 +25,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-FAMILY_BUMPS, FAMILY_RING, FAMILY_RIDGE = 0, 1, 2
+FAMILY_BUMPS, FAMILY_RING, FAMILY_RIDGE, FAMILY_TABLE = 0, 1, 2, 3
 COEF_W, COEF_INV_W = 0, 1
 BMAP_IDENTITY, BMAP_PAPER_1D, BMAP_TABLE = 0, 1, 2
 FP64, FP32_STEP = 0, 1
@@ -80,6 +81,29 @@ def bumps(*bs) -> tuple:
     for b in bs:
         out.extend(float(x) for x in b)
     return tuple(out)
+
+
+def table_params(values) -> tuple:
+    """TABLE family parameters from a [tn, tn] array of ln w (row b = t index)."""
+    v = np.asarray(values, dtype=np.float64)
+    assert v.ndim == 2 and v.shape[0] == v.shape[1] and v.shape[0] >= 2
+    return (float(v.shape[0]),) + tuple(float(x) for x in v.ravel())
+
+
+def smooth_field(tn: int, seed: int = 0, amplitude: float = 1.0, modes: int = 4) -> np.ndarray:
+    """A seeded smooth synthetic field on tn x tn nodes of the unit square (a
+    sum of cosine modes with decaying random amplitudes), e.g. as a tabulated
+    ln w standing in for a density that comes from a numerical solution."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(tn) / (tn - 1.0)
+    S, T = np.meshgrid(x, x, indexing="xy")
+    out = np.zeros((tn, tn))
+    for j in range(modes):
+        for k in range(modes):
+            c = rng.standard_normal() / (1.0 + j * j + k * k)
+            out += c * np.cos(j * np.pi * S + rng.uniform(0, 2 * np.pi)) * np.cos(
+                k * np.pi * T + rng.uniform(0, 2 * np.pi))
+    return amplitude * out
 
 
 # --------------------------------------------------------------- configs ----
