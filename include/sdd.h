@@ -60,10 +60,18 @@ extern "C" {
  * RING : params = [A, cs, ct, k, r0]:
  *        w = 1 + A sech^2(k (|x - c| - r0))             (ring of eq. FiveRingMonitorFunction)
  * RIDGE: params = [A, k, t0, a, f]:
- *        w = 1 + A exp(-k (t - t0 - a sin(2 pi f s))^2)  (eq. MackenzieMonitorFunction) */
+ *        w = 1 + A exp(-k (t - t0 - a sin(2 pi f s))^2)  (eq. MackenzieMonitorFunction)
+ * TABLE: a density given as a table of ln w at the tn x tn nodes
+ *        (a/(tn-1), b/(tn-1)), e.g. from a numerical solution: `table` (host,
+ *        copied at plan creation) holds row b = 0 (t = 0) first, tn values per
+ *        row; w = exp(L) with L the bilinear interpolant of the nodes, and the
+ *        drift is sgn grad L, the interpolant's exact cellwise gradient.  The
+ *        FP32 path kernel reads an FP32 copy through the read-only cache. */
 #define SDD_FAMILY_BUMPS 0
 #define SDD_FAMILY_RING  1
 #define SDD_FAMILY_RIDGE 2
+#define SDD_FAMILY_TABLE 3
+#define SDD_MAX_TABLE    4097
 #define SDD_MAX_BUMPS    6
 #define SDD_MAX_PARAMS   32
 
@@ -134,9 +142,10 @@ typedef struct sdd_plan sdd_plan;
 typedef struct {
     int32_t family;                    /* SDD_FAMILY_* */
     int32_t coef_mode;                 /* SDD_COEF_* */
-    int32_t n_params;                  /* used entries of params */
-    int32_t reserved;
+    int32_t n_params;                  /* used entries of params (0 for TABLE) */
+    int32_t tn;                        /* TABLE: nodes per side, 2..SDD_MAX_TABLE; else 0 */
     double params[SDD_MAX_PARAMS];
+    const double* table;               /* TABLE: host [tn][tn] ln w; else NULL */
 } sdd_density;
 
 typedef struct {
@@ -356,7 +365,9 @@ void sdd_batch_destroy(sdd_batch* batch);
  * Asynchronous on `stream`.
  * Limit: n_nodes * ceil(N / chunk) work items must fit the array (55185);
  * chunk = 0 picks the automatic size, raised up to 8192 until they fit;
- * larger requests fail with SDD_ERR_INVALID_ARG and a message.
+ * larger requests fail with SDD_ERR_INVALID_ARG and a message.  The TABLE
+ * density family is not accepted here (its table reaches the device through
+ * a plan); INVALID_ARG.
  * The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
  * share the array: calls that overlap on the GPU (other streams, other host

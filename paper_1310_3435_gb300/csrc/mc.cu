@@ -256,6 +256,39 @@ struct RidgeF32 {
     }
 };
 
+// TABLE: w = exp(L), L the bilinear interpolant of a table of ln w at the
+// tn x tn nodes (FP32 copy, read through the read-only cache); the drift is
+// sgn grad L, the interpolant's exact cellwise gradient.
+struct TableF32 {
+    static constexpr bool kLight = true;
+    const float* tab;
+    int tn;
+    float m, sdt;
+    __device__ void load(const MeshDev& M)
+    {
+        tab = M.tab32;
+        tn = M.tn;
+        m = (float)(M.tn - 1);
+        sdt = (float)(M.sgn * M.dt);
+    }
+    __device__ __forceinline__ void advance(float s, float t, float& as, float& at,
+                                            float fdt = 1.0f) const
+    {
+        const float x = s * m, y = t * m;
+        const int a = min(max(__float2int_rd(x), 0), tn - 2);
+        const int b = min(max(__float2int_rd(y), 0), tn - 2);
+        const float fa = x - (float)a, fb = y - (float)b;
+        const float* r0 = tab + b * tn + a;
+        const float L00 = __ldg(r0), L10 = __ldg(r0 + 1);
+        const float L01 = __ldg(r0 + tn), L11 = __ldg(r0 + tn + 1);
+        const float Ls = fmaf(fb, (L11 - L01) - (L10 - L00), L10 - L00);
+        const float Lt = fmaf(fa, (L11 - L10) - (L01 - L00), L01 - L00);
+        const float k = (sdt * fdt) * m;
+        as = fmaf(k, Ls, s);
+        at = fmaf(k, Lt, t);
+    }
+};
+
 // ----------------------------------------------------- densities, FP64 ----
 struct BumpsF64 {
     const double* p;
@@ -488,6 +521,34 @@ __device__ void acc_write_slot(const AccSmem& A, int tid, int lane, uint32_t tie
     }
 }
 
+// TABLE, FP64: the same interpolant, the drift sgn grad L in the oracle's
+// order of operations.
+struct TableF64 {
+    const double* tab;
+    int tn;
+    double m, sgn;
+    __device__ void load(const MeshDev& M)
+    {
+        tab = M.tab64;
+        tn = M.tn;
+        m = (double)(M.tn - 1);
+        sgn = M.sgn;
+    }
+    __device__ __forceinline__ void drift(double s, double t, double& bs, double& bt) const
+    {
+        const double x = s * m, y = t * m;
+        const int a = min(max((int)floor(x), 0), tn - 2), b = min(max((int)floor(y), 0), tn - 2);
+        const double fa = x - (double)a, fb = y - (double)b;
+        const double* r0 = tab + b * tn + a;
+        const double L00 = __ldg(r0), L10 = __ldg(r0 + 1);
+        const double L01 = __ldg(r0 + tn), L11 = __ldg(r0 + tn + 1);
+        const double Ls = ((1.0 - fb) * (L10 - L00) + fb * (L11 - L01)) * m;
+        const double Lt = ((1.0 - fa) * (L01 - L00) + fa * (L11 - L10)) * m;
+        bs = sgn * Ls;
+        bt = sgn * Lt;
+    }
+};
+
 template <int PREC> struct RealOf { using T = double; };
 template <> struct RealOf<SDD_FP32_STEP> { using T = float; };
 
@@ -671,6 +732,7 @@ __device__ __forceinline__ void dispatch(const MeshDev& M, const Keys& keys, uin
     switch (M.family) {
         case SDD_FAMILY_RING: run_with<PREC, RingF64>(M, keys, node, chunk, out, A, tid, lane); break;
         case SDD_FAMILY_RIDGE: run_with<PREC, RidgeF64>(M, keys, node, chunk, out, A, tid, lane); break;
+        case SDD_FAMILY_TABLE: run_with<PREC, TableF64>(M, keys, node, chunk, out, A, tid, lane); break;
         default: run_with<PREC, BumpsF64>(M, keys, node, chunk, out, A, tid, lane); break;
     }
 }
@@ -1032,12 +1094,13 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
 
 // Density class of a mesh: a compile-time index for the FP32 path kernel, so
 // each family gets a kernel (and a register allocation) of its own.
-enum FamClass { FC_RING = 0, FC_RIDGE, FC_BUMPS1, FC_BUMPS2, FC_BUMPS3, FC_BUMPS6, FC_ANY };
+enum FamClass { FC_RING = 0, FC_RIDGE, FC_BUMPS1, FC_BUMPS2, FC_BUMPS3, FC_BUMPS6, FC_TABLE, FC_ANY };
 
 __host__ __device__ __forceinline__ int fam_class(int family, int nb)
 {
     if (family == SDD_FAMILY_RING) return FC_RING;
     if (family == SDD_FAMILY_RIDGE) return FC_RIDGE;
+    if (family == SDD_FAMILY_TABLE) return FC_TABLE;
     if (nb <= 1) return FC_BUMPS1;
     if (nb == 2) return FC_BUMPS2;
     if (nb == 3) return FC_BUMPS3;
@@ -1051,6 +1114,7 @@ __device__ __forceinline__ unsigned long long stream_fc(const MeshDev& M, const 
 {
     if constexpr (FC == FC_RING) { RingF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
     if constexpr (FC == FC_RIDGE) { RidgeF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_TABLE) { TableF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
     if constexpr (FC == FC_BUMPS1) { BumpsF32<1> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
     if constexpr (FC == FC_BUMPS2) { BumpsF32<2> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
     if constexpr (FC == FC_BUMPS3) { BumpsF32<3> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
@@ -1073,6 +1137,7 @@ __device__ __forceinline__ unsigned long long dispatch_stream(const MeshDev& M, 
         switch (fam_class(M.family, M.nb)) {
             case FC_RING: return stream_fc<FC_RING, EXPO>(M, keys, item, a, W, lane);
             case FC_RIDGE: return stream_fc<FC_RIDGE, EXPO>(M, keys, item, a, W, lane);
+            case FC_TABLE: return stream_fc<FC_TABLE, EXPO>(M, keys, item, a, W, lane);
             case FC_BUMPS1: return stream_fc<FC_BUMPS1, EXPO>(M, keys, item, a, W, lane);
             case FC_BUMPS2: return stream_fc<FC_BUMPS2, EXPO>(M, keys, item, a, W, lane);
             case FC_BUMPS3: return stream_fc<FC_BUMPS3, EXPO>(M, keys, item, a, W, lane);
@@ -1290,6 +1355,8 @@ void fill_fp32_params(MeshDev& m, const sdd_density& d)
         m.pf[4] = (float)(4.0 * A);
         m.pf[5] = (float)(m.sgn * -8.0 * A * k);
         // u = k (r - r0): the kernel forms r - r0 and folds k into c1 and K
+    } else if (d.family == SDD_FAMILY_TABLE) {
+        m.nb = 0;                                // the table itself is passed by pointer
     } else {
         const double A = d.params[0], k = d.params[1], t0 = d.params[2], a = d.params[3],
                      f = d.params[4];
@@ -1315,6 +1382,7 @@ static PathKernel path_kernel_fp32(bool one, int fc)
         switch (fc) {
             case FC_RING: return k_paths<SDD_FP32_STEP, false, FC_RING, EXPO>;
             case FC_RIDGE: return k_paths<SDD_FP32_STEP, false, FC_RIDGE, EXPO>;
+            case FC_TABLE: return k_paths<SDD_FP32_STEP, false, FC_TABLE, EXPO>;
             case FC_BUMPS1: return k_paths<SDD_FP32_STEP, false, FC_BUMPS1, EXPO>;
             case FC_BUMPS2: return k_paths<SDD_FP32_STEP, false, FC_BUMPS2, EXPO>;
             case FC_BUMPS3: return k_paths<SDD_FP32_STEP, false, FC_BUMPS3, EXPO>;
@@ -1325,6 +1393,7 @@ static PathKernel path_kernel_fp32(bool one, int fc)
     switch (fc) {
         case FC_RING: return k_paths<SDD_FP32_STEP, true, FC_RING, EXPO>;
         case FC_RIDGE: return k_paths<SDD_FP32_STEP, true, FC_RIDGE, EXPO>;
+        case FC_TABLE: return k_paths<SDD_FP32_STEP, true, FC_TABLE, EXPO>;
         case FC_BUMPS1: return k_paths<SDD_FP32_STEP, true, FC_BUMPS1, EXPO>;
         case FC_BUMPS2: return k_paths<SDD_FP32_STEP, true, FC_BUMPS2, EXPO>;
         case FC_BUMPS3: return k_paths<SDD_FP32_STEP, true, FC_BUMPS3, EXPO>;

@@ -134,7 +134,19 @@ double host_coef(const sdd_density& d, double s, double t)
 {
     const double* p = d.params;
     double w;
-    if (d.family == SDD_FAMILY_RING) {
+    if (d.family == SDD_FAMILY_TABLE) {
+        const int tn = d.tn;
+        const double* T = d.table;
+        const double m = (double)(tn - 1);
+        const double x = s * m, y = t * m;
+        const int a = std::min(std::max((int)std::floor(x), 0), tn - 2);
+        const int b = std::min(std::max((int)std::floor(y), 0), tn - 2);
+        const double fa = x - (double)a, fb = y - (double)b;
+        const double L00 = T[b * tn + a], L10 = T[b * tn + a + 1];
+        const double L01 = T[(b + 1) * tn + a], L11 = T[(b + 1) * tn + a + 1];
+        w = std::exp((1.0 - fb) * ((1.0 - fa) * L00 + fa * L10) +
+                     fb * ((1.0 - fa) * L01 + fa * L11));
+    } else if (d.family == SDD_FAMILY_RING) {
         const double ds = s - p[1], dtt = t - p[2];
         const double u = p[3] * (std::sqrt(ds * ds + dtt * dtt) - p[4]);
         const double e = std::exp(-2.0 * std::fabs(u));
@@ -175,6 +187,13 @@ int validate_density(const sdd_density* d)
             if (q[3] < 0 || q[4] < 0) return fail(SDD_ERR_INVALID_ARG, "BUMPS: ks, kt must be >= 0");
             if (q[0] <= -1.0 / nb) return fail(SDD_ERR_INVALID_ARG, "BUMPS: w must stay positive");
         }
+    } else if (d->family == SDD_FAMILY_TABLE) {
+        if (d->tn < 2 || d->tn > SDD_MAX_TABLE)
+            return fail(SDD_ERR_INVALID_ARG, "TABLE: tn must be in [2, SDD_MAX_TABLE]");
+        if (!d->table) return fail(SDD_ERR_INVALID_ARG, "TABLE: table is NULL");
+        for (int64_t q = 0; q < (int64_t)d->tn * d->tn; ++q)
+            if (!std::isfinite(d->table[q]) || std::fabs(d->table[q]) > 700.0)
+                return fail(SDD_ERR_INVALID_ARG, "TABLE: ln w must be finite, |ln w| <= 700");
     } else if (d->family == SDD_FAMILY_RING || d->family == SDD_FAMILY_RIDGE) {
         if (d->n_params < 5) return fail(SDD_ERR_INVALID_ARG, "RING/RIDGE need 5 params");
         if (d->params[0] <= -1.0) return fail(SDD_ERR_INVALID_ARG, "w must stay positive");
@@ -243,7 +262,8 @@ int alloc_solve_buffers(sdd_plan* p, cudaStream_t stream)
 int ensure_coefs(sdd_plan* p, cudaStream_t stream)
 {
     if (p->coefs_ready) return SDD_OK;
-    int rc = launch_edge_coefs(p->n, p->dens.family, p->dens.coef_mode, p->dens.params, p->d_cx,
+    int rc = launch_edge_coefs(p->n, p->dens.family, p->dens.coef_mode, p->dens.params,
+                               p->d_tab64, p->dens.tn, p->d_cx,
                                p->d_cy, p->d_cxf, p->d_cyf, stream);
     if (rc) return rc;
     p->coefs_ready = true;
@@ -324,6 +344,9 @@ void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
     m.nodes = p->d_nodes;
     m.edges = p->d_edges;
     fill_fp32_params(m, p->dens);
+    m.tab64 = p->d_tab64;
+    m.tab32 = p->d_tab32;
+    m.tn = p->dens.tn;
 }
 
 // Builds the mesh record and launches the path kernel + reduction.
@@ -735,6 +758,13 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
     p->sy = sy;
     p->dens = *dens;
     for (int q = dens->n_params; q < SDD_MAX_PARAMS; ++q) p->dens.params[q] = 0.0;
+    if (dens->family == SDD_FAMILY_TABLE) {               // the plan keeps its own copy
+        p->h_table.assign(dens->table, dens->table + (size_t)dens->tn * dens->tn);
+        p->dens.table = p->h_table.data();
+    } else {
+        p->dens.table = nullptr;
+        p->dens.tn = 0;
+    }
     p->bmap_mode = bmap->mode;
     p->ix = interface_lines(n, sx);
     p->iy = interface_lines(n, sy);
@@ -806,13 +836,23 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
     {
         AllocOn on(ss);
         if ((rc = dev_alloc(&p->d_nodes, (size_t)std::max<int64_t>(p->n_nodes, 1))) ||
-            (rc = dev_alloc(&p->d_edges, p->h_edges.size()))) {
+            (rc = dev_alloc(&p->d_edges, p->h_edges.size())) ||
+            (!p->h_table.empty() && ((rc = dev_alloc(&p->d_tab64, p->h_table.size())) ||
+                                     (rc = dev_alloc(&p->d_tab32, p->h_table.size()))))) {
             sdd_plan_destroy(p);
             return rc;
         }
     }
+    std::vector<float> tab32(p->h_table.begin(), p->h_table.end());
     cudaError_t ce = cudaSuccess;
-    if (p->n_nodes > 0)
+    if (!p->h_table.empty()) {
+        ce = cudaMemcpyAsync(p->d_tab64, p->h_table.data(), p->h_table.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, ss);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(p->d_tab32, tab32.data(), tab32.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, ss);
+    }
+    if (ce == cudaSuccess && p->n_nodes > 0)
         ce = cudaMemcpyAsync(p->d_nodes, p->h_nodes.data(), p->h_nodes.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, ss);
     if (ce == cudaSuccess)
@@ -991,6 +1031,8 @@ void sdd_plan_destroy(sdd_plan* p)
     const cudaStream_t fs = p->have_mc || p->last_stream ? p->last_stream : setup_stream();
     dev_free(p->d_nodes, fs);
     dev_free(p->d_edges, fs);
+    dev_free(p->d_tab64, fs);
+    dev_free(p->d_tab32, fs);
     dev_free(p->d_queue, fs);
     dev_free(p->d_slots, fs);
     dev_free(p->d_sums, fs);
@@ -1118,7 +1160,8 @@ int sdd_mesh_quality(sdd_plan* p, const double* mesh, const double* ref, sdd_qua
         }
         if (!p->d_quality && (rc = dev_alloc(&p->d_quality, 1))) return rc;
     }
-    rc = launch_quality(p->n, p->dens.family, p->dens.params, dm, dr, p->d_quality, stream);
+    rc = launch_quality(p->n, p->dens.family, p->dens.params, p->d_tab64, p->dens.tn, dm, dr,
+                        p->d_quality, stream);
     if (rc) return rc;
     QualityDev q;
     SDD_CUDA(cudaMemcpyAsync(&q, p->d_quality, sizeof(q), cudaMemcpyDeviceToHost, stream));
@@ -1592,6 +1635,10 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
         return fail(SDD_ERR_INVALID_ARG, "nodes, edges and mean are required");
     int rc = validate_density(dens);
     if (rc) return rc;
+    if (dens->family == SDD_FAMILY_TABLE)
+        return fail(SDD_ERR_INVALID_ARG,
+                    "the allocation-free entry point takes the analytic families only "
+                    "(a TABLE density is copied to the device by a plan)");
     if ((rc = validate_mc(mc))) return rc;
     if (!is_device_ptr(nodes) || !is_device_ptr(edges) || !is_device_ptr(mean) ||
         (stderr_ && !is_device_ptr(stderr_)))

@@ -66,6 +66,10 @@ struct MeshDev {
     McStatsDev* stats;      // out
     float pf[48];           // FP32-stepping parameters, pre-transformed per family
     double pd[32];          // raw parameters (FP64 stepping)
+    const double* tab64;    // TABLE family: [tn][tn] ln w (FP64 stepping)
+    const float* tab32;     // and its FP32 copy (FP32 stepping)
+    int32_t tn;
+    int32_t pad1;
 };
 
 // Partial sums of one work item (one chunk of paths of one node).
@@ -103,7 +107,7 @@ struct McArgs {
 // kernel per class; kFamAny selects the kernel that handles every class) plus
 // KC_EXPO for exponential time stepping.  FP64 stepping has one kernel.
 int mesh_kernel_class(int family, int nb, int stepper);
-constexpr int kFamAny = 6;
+constexpr int kFamAny = 7;
 constexpr int KC_EXPO = 8;
 
 // Interpolated interface node of a few-point interface (§3.6): value =
@@ -124,8 +128,8 @@ struct QualityDev {
     double q_sum, q_ref_sum;
     unsigned long long folds, ref_folds, l_inf_bits;
 };
-int launch_quality(int n, int family, const double* params, const double* u, const double* ref,
-                   QualityDev* d_out, cudaStream_t stream);
+int launch_quality(int n, int family, const double* params, const double* tab, int tn,
+                   const double* u, const double* ref, QualityDev* d_out, cudaStream_t stream);
 
 // Perona-Malik smoothing of the mesh u [n][n][2] (device), `steps` FTCS steps
 // ping-ponged with `scratch` (device, same size); the result ends in u.
@@ -172,8 +176,8 @@ struct SubStat {
 };
 
 // c at edge midpoints (FP64 and FP32 copies) for one mesh.
-int launch_edge_coefs(int n, int family, int coef_mode, const double* params, double* cx,
-                      double* cy, float* cxf, float* cyf, cudaStream_t stream);
+int launch_edge_coefs(int n, int family, int coef_mode, const double* params, const double* tab,
+                      int tn, double* cx, double* cy, float* cxf, float* cyf, cudaStream_t stream);
 // Boundary tables + interface values into the mesh, Coons-patch start values
 // in the subdomain interiors.
 int launch_fill_mesh(int n, const double* edges, const int2* nodes, int64_t n_nodes,
@@ -225,6 +229,9 @@ struct sdd_plan {
 
     int2* d_nodes = nullptr;
     double* d_edges = nullptr;
+    std::vector<double> h_table;           // TABLE density: [tn][tn] ln w (dens.table points here)
+    double* d_tab64 = nullptr;
+    float* d_tab32 = nullptr;
 
     // Monte Carlo
     unsigned long long* d_queue = nullptr;

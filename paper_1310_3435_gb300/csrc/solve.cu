@@ -30,12 +30,28 @@ namespace {
 constexpr int SOLVE_THREADS_DEFAULT = 1024;
 
 // ------------------------------------------------------ coefficients ----
-// c(s,t) = w or 1/w for the three density families, FP64.
-__device__ double coef64(int family, int coef_mode, const double* __restrict__ p, double s,
-                         double t)
+// Bilinear interpolant of a table of ln w at (s,t) (TABLE family): the cell
+// holding (s,t), the last one on the upper sides.
+__device__ double table_ln_w(const double* __restrict__ T, int tn, double s, double t)
+{
+    const double m = (double)(tn - 1);
+    const double x = s * m, y = t * m;
+    const int a = min(max((int)floor(x), 0), tn - 2), b = min(max((int)floor(y), 0), tn - 2);
+    const double fa = x - (double)a, fb = y - (double)b;
+    const double L00 = __ldg(T + b * tn + a), L10 = __ldg(T + b * tn + a + 1);
+    const double L01 = __ldg(T + (b + 1) * tn + a), L11 = __ldg(T + (b + 1) * tn + a + 1);
+    return (1.0 - fb) * ((1.0 - fa) * L00 + fa * L10) + fb * ((1.0 - fa) * L01 + fa * L11);
+}
+
+// c(s,t) = w or 1/w for the density families, FP64 (tab, tn: the TABLE
+// family's device table).
+__device__ double coef64(int family, int coef_mode, const double* __restrict__ p,
+                         const double* __restrict__ tab, int tn, double s, double t)
 {
     double w;
-    if (family == SDD_FAMILY_RING) {
+    if (family == SDD_FAMILY_TABLE) {
+        w = exp(table_ln_w(tab, tn, s, t));
+    } else if (family == SDD_FAMILY_RING) {
         const double ds = s - p[1], dtt = t - p[2];
         const double u = p[3] * (sqrt(ds * ds + dtt * dtt) - p[4]);
         const double e = exp(-2.0 * fabs(u));
@@ -59,8 +75,9 @@ __device__ double coef64(int family, int coef_mode, const double* __restrict__ p
 }
 
 struct CoefArgs {
-    int n, family, coef_mode;
+    int n, family, coef_mode, tn;
     double p[SDD_MAX_PARAMS];
+    const double* tab;
 };
 
 // cx[j][i] = c((i+1/2)h, jh), i < n-1;  cy[j][i] = c(ih, (j+1/2)h), j < n-1.
@@ -74,13 +91,15 @@ __global__ void k_edge_coefs(CoefArgs a, double* __restrict__ cx, double* __rest
     const double h = 1.0 / (double)(n - 1);
     if (g < m) {
         const int j = (int)(g / (n - 1)), i = (int)(g % (n - 1));
-        const double c = coef64(a.family, a.coef_mode, a.p, ((double)i + 0.5) * h, (double)j / (double)(n - 1));
+        const double c = coef64(a.family, a.coef_mode, a.p, a.tab, a.tn, ((double)i + 0.5) * h,
+                                (double)j / (double)(n - 1));
         cx[g] = c;
         cxf[g] = (float)c;
     } else {
         const int64_t q = g - m;
         const int j = (int)(q / n), i = (int)(q % n);
-        const double c = coef64(a.family, a.coef_mode, a.p, (double)i / (double)(n - 1), ((double)j + 0.5) * h);
+        const double c = coef64(a.family, a.coef_mode, a.p, a.tab, a.tn, (double)i / (double)(n - 1),
+                                ((double)j + 0.5) * h);
         cy[q] = c;
         cyf[q] = (float)c;
     }
@@ -512,8 +531,9 @@ __device__ __forceinline__ bool cell_q(const double2* __restrict__ u, int n, int
 }
 
 struct QualityArgs {
-    int n, family;
+    int n, family, tn;
     double p[SDD_MAX_PARAMS];
+    const double* tab;
 };
 
 __global__ void __launch_bounds__(256) k_quality(QualityArgs a, const double2* __restrict__ u,
@@ -538,8 +558,8 @@ __global__ void __launch_bounds__(256) k_quality(QualityArgs a, const double2* _
         }
         if (ref) {
             const double2 x = u[g], y = ref[g];
-            linf = fmax(linf, fabs(coef64(a.family, SDD_COEF_W, a.p, x.x, x.y) -
-                                   coef64(a.family, SDD_COEF_W, a.p, y.x, y.y)));
+            linf = fmax(linf, fabs(coef64(a.family, SDD_COEF_W, a.p, a.tab, a.tn, x.x, x.y) -
+                                   coef64(a.family, SDD_COEF_W, a.p, a.tab, a.tn, y.x, y.y)));
         }
     }
     (void)cells;
@@ -598,12 +618,14 @@ __global__ void __launch_bounds__(256) k_pm_step(int n, const double2* __restric
 
 }  // namespace
 
-int launch_quality(int n, int family, const double* params, const double* u, const double* ref,
-                   QualityDev* d_out, cudaStream_t stream)
+int launch_quality(int n, int family, const double* params, const double* tab, int tn,
+                   const double* u, const double* ref, QualityDev* d_out, cudaStream_t stream)
 {
     QualityArgs a;
     a.n = n;
     a.family = family;
+    a.tab = tab;
+    a.tn = tn;
     for (int q = 0; q < SDD_MAX_PARAMS; ++q) a.p[q] = params[q];
     SDD_CUDA(cudaMemsetAsync(d_out, 0, sizeof(QualityDev), stream));
     const int64_t nodes = (int64_t)n * n;
@@ -637,13 +659,15 @@ int launch_smooth(int n, double* u, double* scratch, int steps, double dt, doubl
     return SDD_OK;
 }
 
-int launch_edge_coefs(int n, int family, int coef_mode, const double* params, double* cx,
-                      double* cy, float* cxf, float* cyf, cudaStream_t stream)
+int launch_edge_coefs(int n, int family, int coef_mode, const double* params, const double* tab,
+                      int tn, double* cx, double* cy, float* cxf, float* cyf, cudaStream_t stream)
 {
     CoefArgs a;
     a.n = n;
     a.family = family;
     a.coef_mode = coef_mode;
+    a.tab = tab;
+    a.tn = tn;
     for (int q = 0; q < SDD_MAX_PARAMS; ++q) a.p[q] = params[q];
     const int64_t total = 2 * (int64_t)n * (n - 1);
     k_edge_coefs<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a, cx, cy, cxf, cyf);

@@ -27,7 +27,8 @@ SDD_ERR_CUDA = -3
 SDD_ERR_NOT_CONVERGED = -4
 SDD_ERR_NO_DEVICE = -5
 
-SDD_FAMILY_BUMPS, SDD_FAMILY_RING, SDD_FAMILY_RIDGE = 0, 1, 2
+SDD_FAMILY_BUMPS, SDD_FAMILY_RING, SDD_FAMILY_RIDGE, SDD_FAMILY_TABLE = 0, 1, 2, 3
+SDD_MAX_TABLE = 4097
 SDD_MAX_BUMPS, SDD_MAX_PARAMS = 6, 32
 SDD_COEF_W, SDD_COEF_INV_W = 0, 1
 SDD_BMAP_IDENTITY, SDD_BMAP_PAPER_1D, SDD_BMAP_TABLE = 0, 1, 2
@@ -46,8 +47,9 @@ class SddError(RuntimeError):
 
 class sdd_density(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int32), ("coef_mode", ctypes.c_int32),
-                ("n_params", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("params", ctypes.c_double * SDD_MAX_PARAMS)]
+                ("n_params", ctypes.c_int32), ("tn", ctypes.c_int32),
+                ("params", ctypes.c_double * SDD_MAX_PARAMS),
+                ("table", ctypes.POINTER(ctypes.c_double))]
 
 
 class sdd_bmap(ctypes.Structure):
@@ -207,9 +209,22 @@ def _stream(s):
 
 # ---------------------------------------------------------- C-named calls --
 def make_density(family: int, params, coef_mode: int = SDD_COEF_W) -> sdd_density:
+    """Density record.  SDD_FAMILY_TABLE takes params = (tn, tn*tn values of
+    ln w, row by row in t); the record then points at a numpy copy of the
+    table, kept alive as the record's `_table` (the plan copies it)."""
     d = sdd_density()
     d.family = int(family)
     d.coef_mode = int(coef_mode)
+    if d.family == SDD_FAMILY_TABLE:
+        q = np.asarray(params, dtype=np.float64).ravel()
+        tn = int(q[0])
+        if q.size != 1 + tn * tn:
+            raise ValueError("TABLE params must be (tn, tn*tn values of ln w)")
+        d._table = np.ascontiguousarray(q[1:])
+        d.tn = tn
+        d.n_params = 0
+        d.table = d._table.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        return d
     p = [float(x) for x in params]
     if len(p) > SDD_MAX_PARAMS:
         raise ValueError("at most %d density parameters" % SDD_MAX_PARAMS)
