@@ -50,8 +50,14 @@ OPS_BRIDGE_EXTRA = 4.5
 OPS_BRIDGE_EXPO_EXTRA = 1.5
 
 
-def ops_per_step(stepper: int, exit_test: int) -> float:
-    ops = float(OPS_PER_STEP_RING_FP32)
+# Drift evaluations other than the ring's 22: the tabulated density (cell
+# coordinates, clamps and weights 10, the cell index 2, one 16-byte read, the
+# two gradient components 2, the update 2) = 17.
+DRIFT_OPS = {W.FAMILY_RING: 22, W.FAMILY_TABLE: 17}
+
+
+def ops_per_step(stepper: int, exit_test: int, family: int = W.FAMILY_RING) -> float:
+    ops = float(OPS_PER_STEP_RING_FP32) - DRIFT_OPS[W.FAMILY_RING] + DRIFT_OPS.get(family, 22)
     if stepper == W.STEP_EXPONENTIAL:
         ops += OPS_EXPO_EXTRA
     if exit_test == W.EXIT_BRIDGE:
@@ -184,10 +190,18 @@ def bench_spec(args, seed=None):
         over["stepper"] = W.STEP_EXPONENTIAL
     if args.exit_test == "bridge":
         over["exit_test"] = W.EXIT_BRIDGE
+    if args.table_tn:
+        # a tabulated density in place of the analytic one: a seeded smooth
+        # field of ln w on table_tn x table_tn nodes
+        over["family"] = W.FAMILY_TABLE
+        over["params"] = W.table_params(W.smooth_field(args.table_tn, seed=1, amplitude=2.0))
     spec = W.MeshSpec(**{**spec.__dict__, **over})
-    if spec.stepper != W.STEP_EULER or spec.exit_test != W.EXIT_END_OF_STEP or args.dt:
-        spec = W.MeshSpec(**{**spec.__dict__, "label": "%s, %s steps, %s exit test, dt=%g" % (
-            spec.label.split(" N=")[0], args.stepper, args.exit_test, spec.dt)})
+    if (spec.stepper != W.STEP_EULER or spec.exit_test != W.EXIT_END_OF_STEP or args.dt
+            or args.table_tn):
+        dens = "table %dx%d" % (args.table_tn, args.table_tn) if args.table_tn else ""
+        spec = W.MeshSpec(**{**spec.__dict__, "label": "%s%s, %s steps, %s exit test, dt=%g" % (
+            spec.label.split(" N=")[0].replace("ring", dens) if dens else spec.label.split(" N=")[0],
+            "", args.stepper, args.exit_test, spec.dt)})
     return spec
 
 
@@ -347,7 +361,7 @@ def run_native(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * 128 * sm_clock_max * 1e6 / 1e9          # Gop/s
     t_mc = sum(ms_mc) / len(ms_mc) / 1000.0
-    ops = ops_per_step(spec.stepper, spec.exit_test)
+    ops = ops_per_step(spec.stepper, spec.exit_test, spec.family)
     achieved = ops * path_steps / t_mc / 1e9
     line = {
         "mc_path_steps_per_s": achieved_steps_per_s(path_steps, t_mc),
@@ -372,7 +386,8 @@ def run_native(args):
                      "frac": achieved / alu_peak, "traffic": path_kernel_traffic(spec),
                      "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of one "
                                       "launch (ncu), bytes; null if the kernel source changed",
-                     "kernel": "k_paths<FP32> (+k_reduce)",
+                     "kernel": "k_paths<FP32, %s> (+k_reduce)" % (
+                         "table" if spec.family == W.FAMILY_TABLE else "ring"),
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                                    % (sms, sm_clock_max, peak_kind),
                      "ops_per_path_step": ops},
@@ -697,6 +712,8 @@ def main(argv=None):
                     help="time stepping of the paths (exponential: mean step dt)")
     ap.add_argument("--exit-test", choices=["end", "bridge"], default="end")
     ap.add_argument("--dt", type=float, default=0.0, help="override the workload's (mean) step")
+    ap.add_argument("--table-tn", type=int, default=0,
+                    help="replace the density by a tabulated ln w on this many nodes per side")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
     ap.add_argument("--n-max", type=int, default=1025)
     ap.add_argument("--target-stderr", type=float, default=1e-3)

@@ -257,35 +257,33 @@ struct RidgeF32 {
 };
 
 // TABLE: w = exp(L), L the bilinear interpolant of a table of ln w at the
-// tn x tn nodes (FP32 copy, read through the read-only cache); the drift is
-// sgn grad L, the interpolant's exact cellwise gradient.
+// tn x tn nodes; the drift is sgn grad L, the interpolant's exact cellwise
+// gradient: with (fa, fb) the position in its cell, dL/ds = c1 + c3 fb and
+// dL/dt = c2 + c3 fa, (c1, c2, c3) one 16-byte record per cell read through
+// the read-only cache (one gather per drift evaluation).  The position is
+// clamped into [0, tn-1) cells; the cell index is formed in FP32 (exact for
+// tn <= 4097).
 struct TableF32 {
     static constexpr bool kLight = true;
-    const float* tab;
-    int tn;
-    float m, sdt;
+    const float4* cell;
+    float m, xmax, sdt;
     __device__ void load(const MeshDev& M)
     {
-        tab = M.tab32;
-        tn = M.tn;
+        cell = M.cell32;
         m = (float)(M.tn - 1);
+        xmax = __int_as_float(__float_as_int(m) - 1);      // largest float below tn - 1
         sdt = (float)(M.sgn * M.dt);
     }
     __device__ __forceinline__ void advance(float s, float t, float& as, float& at,
                                             float fdt = 1.0f) const
     {
-        const float x = s * m, y = t * m;
-        const int a = min(max(__float2int_rd(x), 0), tn - 2);
-        const int b = min(max(__float2int_rd(y), 0), tn - 2);
-        const float fa = x - (float)a, fb = y - (float)b;
-        const float* r0 = tab + b * tn + a;
-        const float L00 = __ldg(r0), L10 = __ldg(r0 + 1);
-        const float L01 = __ldg(r0 + tn), L11 = __ldg(r0 + tn + 1);
-        const float Ls = fmaf(fb, (L11 - L01) - (L10 - L00), L10 - L00);
-        const float Lt = fmaf(fa, (L11 - L10) - (L01 - L00), L01 - L00);
-        const float k = (sdt * fdt) * m;
-        as = fmaf(k, Ls, s);
-        at = fmaf(k, Lt, t);
+        const float x = fminf(fmaxf(s * m, 0.0f), xmax), y = fminf(fmaxf(t * m, 0.0f), xmax);
+        const float xf = floorf(x), yf = floorf(y);
+        const float fa = x - xf, fb = y - yf;
+        const float4 c = __ldg(cell + __float2int_rz(fmaf(yf, m, xf)));
+        const float k = sdt * fdt;
+        as = fmaf(k, fmaf(c.z, fb, c.x), s);
+        at = fmaf(k, fmaf(c.z, fa, c.y), t);
     }
 };
 

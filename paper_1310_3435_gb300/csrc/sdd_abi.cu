@@ -345,7 +345,7 @@ void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
     m.edges = p->d_edges;
     fill_fp32_params(m, p->dens);
     m.tab64 = p->d_tab64;
-    m.tab32 = p->d_tab32;
+    m.cell32 = p->d_cell32;
     m.tn = p->dens.tn;
 }
 
@@ -837,19 +837,36 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
         AllocOn on(ss);
         if ((rc = dev_alloc(&p->d_nodes, (size_t)std::max<int64_t>(p->n_nodes, 1))) ||
             (rc = dev_alloc(&p->d_edges, p->h_edges.size())) ||
-            (!p->h_table.empty() && ((rc = dev_alloc(&p->d_tab64, p->h_table.size())) ||
-                                     (rc = dev_alloc(&p->d_tab32, p->h_table.size()))))) {
+            (!p->h_table.empty() &&
+             ((rc = dev_alloc(&p->d_tab64, p->h_table.size())) ||
+              (rc = dev_alloc(&p->d_cell32, (size_t)(p->dens.tn - 1) * (p->dens.tn - 1)))))) {
             sdd_plan_destroy(p);
             return rc;
         }
     }
-    std::vector<float> tab32(p->h_table.begin(), p->h_table.end());
+    // FP32 stepping reads one 16-byte record per cell: the bilinear
+    // interpolant's gradient coefficients, scaled by 1/spacing (FP64, rounded)
+    std::vector<float4> cells;
+    if (!p->h_table.empty()) {
+        const int tn = p->dens.tn;
+        const double m = (double)(tn - 1);
+        const double* T = p->h_table.data();
+        cells.resize((size_t)(tn - 1) * (tn - 1));
+        for (int b = 0; b < tn - 1; ++b)
+            for (int a = 0; a < tn - 1; ++a) {
+                const double L00 = T[b * tn + a], L10 = T[b * tn + a + 1];
+                const double L01 = T[(b + 1) * tn + a], L11 = T[(b + 1) * tn + a + 1];
+                cells[(size_t)b * (tn - 1) + a] =
+                    make_float4((float)((L10 - L00) * m), (float)((L01 - L00) * m),
+                                (float)((L11 - L10 - L01 + L00) * m), 0.0f);
+            }
+    }
     cudaError_t ce = cudaSuccess;
     if (!p->h_table.empty()) {
         ce = cudaMemcpyAsync(p->d_tab64, p->h_table.data(), p->h_table.size() * sizeof(double),
                              cudaMemcpyHostToDevice, ss);
         if (ce == cudaSuccess)
-            ce = cudaMemcpyAsync(p->d_tab32, tab32.data(), tab32.size() * sizeof(float),
+            ce = cudaMemcpyAsync(p->d_cell32, cells.data(), cells.size() * sizeof(float4),
                                  cudaMemcpyHostToDevice, ss);
     }
     if (ce == cudaSuccess && p->n_nodes > 0)
@@ -1032,7 +1049,7 @@ void sdd_plan_destroy(sdd_plan* p)
     dev_free(p->d_nodes, fs);
     dev_free(p->d_edges, fs);
     dev_free(p->d_tab64, fs);
-    dev_free(p->d_tab32, fs);
+    dev_free(p->d_cell32, fs);
     dev_free(p->d_queue, fs);
     dev_free(p->d_slots, fs);
     dev_free(p->d_sums, fs);

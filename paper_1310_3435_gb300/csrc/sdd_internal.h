@@ -67,7 +67,8 @@ struct MeshDev {
     float pf[48];           // FP32-stepping parameters, pre-transformed per family
     double pd[32];          // raw parameters (FP64 stepping)
     const double* tab64;    // TABLE family: [tn][tn] ln w (FP64 stepping)
-    const float* tab32;     // and its FP32 copy (FP32 stepping)
+    const float4* cell32;   // FP32 stepping: per cell (c1, c2, c3, 0) with L = c0 + (c1 fa +
+                            // c2 fb + c3 fa fb) / (tn-1) in the cell's local coordinates
     int32_t tn;
     int32_t pad1;
 };
@@ -231,7 +232,7 @@ struct sdd_plan {
     double* d_edges = nullptr;
     std::vector<double> h_table;           // TABLE density: [tn][tn] ln w (dens.table points here)
     double* d_tab64 = nullptr;
-    float* d_tab32 = nullptr;
+    float4* d_cell32 = nullptr;            // FP32 per-cell gradient coefficients
 
     // Monte Carlo
     unsigned long long* d_queue = nullptr;
