@@ -590,6 +590,78 @@ def run_precision(args):
     return 0
 
 
+def five_ring_ln_rho(tn: int, alpha: float = 0.2, R: float = 30.0) -> np.ndarray:
+    """ln of the paper's five-ring arc-length monitor (eq. FiveRingMonitorFunction,
+    rho = sqrt(1 + alpha |grad u|^2), u a sum of five tanh rings on [-1,1]^2) at
+    the tn x tn nodes of the unit square, through x = 2s - 1, y = 2t - 1."""
+    g = np.arange(tn) / (tn - 1.0)
+    S, T = np.meshgrid(g, g, indexing="xy")
+    x, y = 2.0 * S - 1.0, 2.0 * T - 1.0
+    ux = np.zeros_like(x)
+    uy = np.zeros_like(x)
+    for cx, cy in ((0.0, 0.0), (0.5, 0.5), (0.5, -0.5), (-0.5, 0.5), (-0.5, -0.5)):
+        q = (x - cx) ** 2 + (y - cy) ** 2 - 0.125
+        sech2 = 1.0 / np.cosh(R * q) ** 2
+        ux += R * sech2 * 2.0 * (x - cx)
+        uy += R * sech2 * 2.0 * (y - cy)
+    return 0.5 * np.log1p(alpha * (ux * ux + uy * uy))
+
+
+def run_paper_performance(args):
+    """The paper's performance study (§5, Table 5) in its workload shape on one
+    GB300: the five-ring arc-length monitor (tabulated on 1025 x 1025 nodes,
+    w = 1/rho), 4 x 4 subdomains, n = 37 ... 197, N = 5000, exponential steps
+    with the boundary test at the paper's lambda = 1000 on [-1,1]^2 (mean step
+    1/(4 lambda) on the unit square), FP32 stepping; the Monte Carlo at every
+    interface node and at the extrema placement.  T_stoc and T_sub per mesh
+    are CUDA-event times after a warm-up, beside the paper's 16-core times."""
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    torch.cuda.set_device(0)
+    params = W.table_params(five_ring_ln_rho(1025))
+    paper = {37: (5.47, 0.00), 77: (7.56, 0.02), 117: (8.81, 0.08), 157: (8.88, 0.21),
+             197: (9.06, 0.47)}
+    stream = torch.cuda.Stream()
+    rows = []
+    for n in (37, 77, 117, 157, 197):
+        for place in (N.SDD_PLACE_ALL, N.SDD_PLACE_EXTREMA):
+            spec = W.MeshSpec(n=n, sx=4, sy=4, family=W.FAMILY_TABLE, params=params,
+                              coef_mode=W.COEF_INV_W, bmap_mode=W.BMAP_PAPER_1D, paths=5000,
+                              dt=1.0 / 4000.0, precision=W.FP32_STEP, stepper=W.STEP_EXPONENTIAL,
+                              exit_test=W.EXIT_BRIDGE, solver=W.SOLVER_CG_FP32_REFINE, tol=1e-10)
+            with N.Plan(spec) as P:
+                N.sdd_plan_set_placement(P.handle, place, 0)
+                _, n_mc = N.sdd_plan_placement(P.handle)
+                mean = torch.zeros((P.n_nodes, 2), dtype=torch.float64, device="cuda")
+                mesh = torch.zeros((n, n, 2), dtype=torch.float64, device="cuda")
+                mc, sp = P.mc_params(), P.solve_params()
+                t_mc, t_sub = [], []
+                for rep in range(4):
+                    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    e[0].record(stream)
+                    N.sdd_interface_mc(P.handle, mc, mean, None, want_stats=False, stream=stream)
+                    e[1].record(stream)
+                    N.sdd_subdomain_solve(P.handle, mean, sp, mesh, want_stats=False,
+                                          stream=stream)
+                    e[2].record(stream)
+                    stream.synchronize()
+                    if rep:                                   # the first run warms up
+                        t_mc.append(e[0].elapsed_time(e[1]) / 1000.0)
+                        t_sub.append(e[1].elapsed_time(e[2]) / 1000.0)
+                st = N.sdd_plan_last_mc_stats(P.handle)
+            rows.append({"n": n, "placement": "all" if place == N.SDD_PLACE_ALL else "extrema",
+                         "mc_nodes": n_mc, "path_steps": int(st.path_steps),
+                         "T_stoc_s": float(np.median(t_mc)), "T_sub_s": float(np.median(t_sub)),
+                         "paper_T_stoc_s": paper[n][0], "paper_T_sub_s": paper[n][1],
+                         "non_exits": int(st.non_exits)})
+    print(json.dumps({"metric": "T_stoc, T_sub of the paper's performance study (Table 5 shape)",
+                      "workload": "five-ring arc-length monitor (table 1025^2), 4x4, N=5000, "
+                                  "exponential steps lambda=1000 on [-1,1]^2, boundary test, FP32",
+                      "paper_hardware": "16-core CPU machine (the paper's Table 5)",
+                      "rows": rows}))
+    return 0
+
+
 def run_quality(args):
     """Mesh-quality report on the paper's running example (eq.
     MonitorFunctionRunningExample: rho = 1 + 15 exp(-50 (x - 3/4)^2 - 50 (y -
@@ -712,6 +784,8 @@ def main(argv=None):
                     help="time stepping of the paths (exponential: mean step dt)")
     ap.add_argument("--exit-test", choices=["end", "bridge"], default="end")
     ap.add_argument("--dt", type=float, default=0.0, help="override the workload's (mean) step")
+    ap.add_argument("--paper-performance", action="store_true",
+                    help="the paper's performance study (five rings, 4x4, n = 37..197)")
     ap.add_argument("--table-tn", type=int, default=0,
                     help="replace the density by a tabulated ln w on this many nodes per side")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0])
@@ -738,6 +812,8 @@ def main(argv=None):
         return run_precision(args)
     if args.quality_report:
         return run_quality(args)
+    if args.paper_performance:
+        return run_paper_performance(args)
     if args.config == "config3":
         return run_batched(args)
     return run_native(args)
