@@ -115,7 +115,8 @@ constexpr double PI_D = 3.14159265358979323846;
 // Box-Muller, FP32.  Uniforms U = (floor(r / 2^9) + 1/2) 2^-23 are exact in
 // FP32 and lie in (0,1); the angle 2 pi U is taken as 2 pi (U - 1/2) + pi,
 // i.e. (cos, sin)(2 pi U) = -(cos, sin)(2 pi (U - 1/2)), which keeps the
-// argument of the hardware sine/cosine in [-pi, pi] (the sign goes into nr).
+// argument of the hardware sine/cosine in [-pi, pi] (the sign goes into nr);
+// the angle's uniform drops the half step (see box_muller_f32_step).
 __device__ __forceinline__ float uniform23(uint32_t r)
 {
     // 1 + floor(r/2^9) 2^-23 in [1,2), minus (1 - 2^-24): exact.
@@ -129,10 +130,13 @@ __device__ __forceinline__ float uniform23(uint32_t r)
 __device__ __forceinline__ void box_muller_f32_step(uint32_t ra, uint32_t rb, float c4dt,
                                                     float& nr, float& cz, float& sz)
 {
-    const float ua = uniform23(ra), ub = uniform23(rb);
+    const float ua = uniform23(ra);
     const float v = c4dt * lg2_approx(ua);                  // -4 dt ln ua > 0
     nr = -sqrt_approx(v);
-    const float ang = TWO_PI_F * (ub - 0.5f);
+    // angle 2 pi (floor(rb / 2^9) 2^-23 - 1/2), exact before the multiply: the
+    // grid of the FP64 angle shifted by half an FP32 step, a fixed rotation by
+    // 2 pi 2^-24 that leaves the distribution of the normal pair unchanged
+    const float ang = TWO_PI_F * (__uint_as_float((rb >> 9) + 0x3f800000u) - 1.5f);
     cz = cos_approx(ang);
     sz = sin_approx(ang);
 }
