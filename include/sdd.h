@@ -243,6 +243,42 @@ int sdd_interface_mc(sdd_plan* plan, const sdd_mc_params* mc, double* mean, doub
 int sdd_interface_mc_sums(sdd_plan* plan, const sdd_mc_params* mc, sdd_node_sums* sums,
                           void* stream);
 
+/* ---- one Monte Carlo run split over calls, and checkpoints of it ----
+ * The estimator's sums are additive over the work items (a chunk of paths of
+ * one node, §2.2; §6 notes the additivity of the expectation), so a run can
+ * stop between items and go on later, on another plan built from the same
+ * request, from a host copy of the items done.  The result is bitwise the
+ * same as one sdd_interface_mc call with the same parameters (no counterpart
+ * in the paper beyond that remark: preemption and recovery for serving).
+ *
+ * sdd_interface_mc_advance runs the next up to max_items work items of the
+ * plan's run for `mc` (a call with other parameters, or after a whole
+ * sdd_interface_mc call, starts a new run); *items_done and *items_total
+ * (may be NULL) receive the progress.  Stream-ordered, asynchronous. */
+int sdd_interface_mc_advance(sdd_plan* plan, const sdd_mc_params* mc, uint64_t max_items,
+                             uint64_t* items_done, uint64_t* items_total, void* stream);
+
+/* Reduces a finished split run (every item done) into the node means and
+ * standard errors, like sdd_interface_mc.  Errors: INVALID_ARG when no run
+ * with these parameters is in progress or items are left. */
+int sdd_interface_mc_finish(sdd_plan* plan, const sdd_mc_params* mc, double* mean,
+                            double* stderr_, sdd_mc_stats* stats, void* stream);
+
+/* Size of a checkpoint of the plan's split run: a header (parameters,
+ * progress, a hash of the plan's grid, density, boundary tables and Monte
+ * Carlo nodes) and the sums of the items done. */
+int sdd_mc_checkpoint_bytes(const sdd_plan* plan, uint64_t* bytes);
+
+/* Writes the checkpoint into host memory `host` of `bytes` bytes (synchronises
+ * `stream`).  Errors: INVALID_ARG (no run in progress, buffer too small). */
+int sdd_mc_checkpoint_save(sdd_plan* plan, void* host, uint64_t bytes, void* stream);
+
+/* Restores a checkpoint into a plan built from the same request, which then
+ * continues with sdd_interface_mc_advance (same parameters) and finishes with
+ * sdd_interface_mc_finish.  Errors: INVALID_ARG (not a checkpoint, another
+ * plan, truncated). */
+int sdd_mc_checkpoint_load(sdd_plan* plan, const void* host, uint64_t bytes, void* stream);
+
 /* Statistics of the plan's last sdd_interface_mc / _sums / sdd_mesh_generate
  * call.  Waits for that call only (an event recorded after it), not for later
  * work on its stream.  After a batch run use sdd_batch_plan_stats. */

@@ -843,7 +843,7 @@ __device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs
             if (!held_valid) {
                 if (have_pending) break;
                 unsigned long long it = 0;
-                if (lane == 0) it = atomicAdd(a.queue, 1ull);
+                if (lane == 0) it = a.item_base + atomicAdd(a.queue, 1ull);
                 it = __shfl_sync(FULL, it, 0);
                 if (it >= a.total_items || it >= mesh_end) {
                     pending = it;
@@ -1185,7 +1185,7 @@ k_paths(const __grid_constant__ McArgs a)
         __shared__ AccSmem acc;
         for (;;) {
             unsigned long long item = 0;
-            if (lane == 0) item = atomicAdd(a.queue, 1ull);
+            if (lane == 0) item = a.item_base + atomicAdd(a.queue, 1ull);
             item = __shfl_sync(FULL, item, 0);
             if (item >= a.total_items) return;
             const MeshDev& M = ONE ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
@@ -1206,7 +1206,7 @@ k_paths(const __grid_constant__ McArgs a)
         __shared__ WarpAcc wacc[MC_THREADS / 32];
         WarpAcc& W = wacc[tid >> 5];
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.queue, 1ull);
+        if (lane == 0) item = a.item_base + atomicAdd(a.queue, 1ull);
         item = __shfl_sync(FULL, item, 0);
         while (item < a.total_items) {
             const MeshDev& M = ONE ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
@@ -1430,7 +1430,7 @@ int mc_grid_blocks(int precision, int kc, bool one, int* blocks, int* threads)
 
 int launch_mc(const McArgs& args, int precision, int kc, cudaStream_t stream)
 {
-    if (args.total_items == 0) return SDD_OK;
+    if (args.total_items <= args.item_base) return SDD_OK;
     const bool one = args.meshes == nullptr;
     int blocks = 0, threads = 0;
     int rc = mc_grid_blocks(precision, kc, one, &blocks, &threads);
@@ -1438,23 +1438,47 @@ int launch_mc(const McArgs& args, int precision, int kc, cudaStream_t stream)
     return launch_mc_sized(args, precision, kc, blocks, stream);
 }
 
-int launch_mc_sized(const McArgs& args, int precision, int kc, int blocks, cudaStream_t stream)
+static int launch_paths_sized(const McArgs& args, int precision, int kc, int blocks,
+                              cudaStream_t stream)
 {
-    if (args.total_items == 0) return SDD_OK;
+    if (args.total_items <= args.item_base) return SDD_OK;
     const bool one = args.meshes == nullptr;
     const int threads = MC_THREADS;
-    const uint64_t max_blocks = (args.total_items * 32 + threads - 1) / threads;
+    const uint64_t max_blocks = ((args.total_items - args.item_base) * 32 + threads - 1) / threads;
     if ((uint64_t)blocks > max_blocks) blocks = (int)max_blocks;
     if (blocks < 1) blocks = 1;
     SDD_CUDA(cudaMemsetAsync(args.queue, 0, sizeof(unsigned long long), stream));
     path_kernel(precision, one, kc)<<<blocks, threads, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
+    return SDD_OK;
+}
+
+int launch_mc_reduce(const McArgs& args, cudaStream_t stream)
+{
+    if (args.total_nodes == 0) return SDD_OK;
     const unsigned rb = (unsigned)((args.total_nodes + 255) / 256);
     k_reduce<<<rb, 256, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();
     return SDD_OK;
+}
+
+int launch_mc_paths(const McArgs& args, int precision, int kc, cudaStream_t stream)
+{
+    if (args.total_items <= args.item_base) return SDD_OK;
+    int blocks = 0;
+    int rc = mc_grid_blocks(precision, kc, args.meshes == nullptr, &blocks, nullptr);
+    if (rc) return rc;
+    return launch_paths_sized(args, precision, kc, blocks, stream);
+}
+
+int launch_mc_sized(const McArgs& args, int precision, int kc, int blocks, cudaStream_t stream)
+{
+    if (args.total_items <= args.item_base) return SDD_OK;
+    int rc = launch_paths_sized(args, precision, kc, blocks, stream);
+    if (rc) return rc;
+    return launch_mc_reduce(args, stream);
 }
 
 }  // namespace sdd

@@ -350,16 +350,57 @@ void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
 }
 
 // Builds the mesh record and launches the path kernel + reduction.
+// Launch record of plan p's Monte Carlo for mc (few-point aware), with the
+// plan's buffers sized for it; `few` tells whether the interface is few-point.
+int mc_args(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stderr_dev,
+            sdd_node_sums* sums_dev, McArgs& a, bool& few, cudaStream_t stream);
+
+// Tail of a Monte Carlo run after the reduction: interpolation of a few-point
+// interface, copies to the caller's device outputs, the plan's bookkeeping.
+int mc_tail(sdd_plan* p, const sdd_mc_params* mc, bool few, double* mean_dev, double* stderr_dev,
+            cudaStream_t stream)
+{
+    int rc;
+    if (few) {
+        if ((rc = launch_interp(p->d_interp, (int64_t)p->h_interp.size(), stream))) return rc;
+        const size_t bytes = (size_t)p->n_nodes * 2 * sizeof(double);
+        if (mean_dev && mean_dev != p->d_mean)
+            SDD_CUDA(cudaMemcpyAsync(mean_dev, p->d_mean, bytes, cudaMemcpyDeviceToDevice, stream));
+        if (stderr_dev && stderr_dev != p->d_stderr)
+            SDD_CUDA(cudaMemcpyAsync(stderr_dev, p->d_stderr, bytes, cudaMemcpyDeviceToDevice, stream));
+    }
+    if (!p->mc_done) SDD_CUDA(cudaEventCreateWithFlags(&p->mc_done, cudaEventDisableTiming));
+    SDD_CUDA(cudaEventRecord(p->mc_done, stream));
+    p->last_paths = mc->paths_per_node;
+    p->have_mc = true;
+    p->last_stream = stream;
+    return SDD_OK;
+}
+
 int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stderr_dev,
            sdd_node_sums* sums_dev, cudaStream_t stream)
 {
     int rc = validate_mc(mc);
     if (rc) return rc;
+    p->resume_active = false;                 // a whole run replaces any split one
     McArgs a;
+    bool few = false;
+    if ((rc = mc_args(p, mc, mean_dev, stderr_dev, sums_dev, a, few, stream))) return rc;
+    SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
+    if ((rc = launch_mc(a, mc->precision, mesh_kernel_class(a.single.family, a.single.nb,
+                                                            a.single.stepper), stream)))
+        return rc;
+    return mc_tail(p, mc, few, mean_dev, stderr_dev, stream);
+}
+
+int mc_args(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stderr_dev,
+            sdd_node_sums* sums_dev, McArgs& a, bool& few, cudaStream_t stream)
+{
+    int rc;
     memset(&a, 0, sizeof(a));
     MeshDev& m = a.single;
     mesh_record(p, mc, m);
-    const bool few = p->n_mc < p->n_nodes;            // few-point interface
+    few = p->n_mc < p->n_nodes;                      // few-point interface
     if (few) {
         m.n_nodes = p->n_mc;
         if (m.chunk == auto_chunk(mc->paths_per_node, p->n_nodes) && !mc->chunk) {
@@ -389,21 +430,6 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     a.total_nodes = (uint64_t)m.n_nodes;
     a.queue = p->d_queue;
     a.slots = p->d_slots;
-    SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
-    if ((rc = launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper), stream))) return rc;
-    if (few) {
-        if ((rc = launch_interp(p->d_interp, (int64_t)p->h_interp.size(), stream))) return rc;
-        const size_t bytes = (size_t)p->n_nodes * 2 * sizeof(double);
-        if (mean_dev && mean_dev != p->d_mean)
-            SDD_CUDA(cudaMemcpyAsync(mean_dev, p->d_mean, bytes, cudaMemcpyDeviceToDevice, stream));
-        if (stderr_dev && stderr_dev != p->d_stderr)
-            SDD_CUDA(cudaMemcpyAsync(stderr_dev, p->d_stderr, bytes, cudaMemcpyDeviceToDevice, stream));
-    }
-    if (!p->mc_done) SDD_CUDA(cudaEventCreateWithFlags(&p->mc_done, cudaEventDisableTiming));
-    SDD_CUDA(cudaEventRecord(p->mc_done, stream));
-    p->last_paths = mc->paths_per_node;
-    p->have_mc = true;
-    p->last_stream = stream;
     return SDD_OK;
 }
 
@@ -952,6 +978,194 @@ int sdd_interface_mc_sums(sdd_plan* p, const sdd_mc_params* mc, sdd_node_sums* s
                                  cudaMemcpyDeviceToHost, stream));
         SDD_CUDA(cudaStreamSynchronize(stream));
     }
+    return SDD_OK;
+}
+
+// ---- a Monte Carlo run split over calls, and its checkpoints ----
+namespace {
+constexpr uint32_t kCheckpointMagic = 0x43444453u;   // "SDDC"
+
+struct CheckpointHeader {
+    uint32_t magic, version;
+    uint64_t n, n_mc, items_total, items_done, slot_bytes, plan_hash;
+    sdd_mc_params mc;
+};
+
+// FNV-1a over what fixes a plan's Monte Carlo: grid, density, boundary tables,
+// Monte Carlo nodes.
+uint64_t plan_hash(const sdd_plan* p)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* data, size_t bytes) {
+        const unsigned char* c = static_cast<const unsigned char*>(data);
+        for (size_t q = 0; q < bytes; ++q) h = (h ^ c[q]) * 1099511628211ull;
+    };
+    mix(&p->n, sizeof(p->n));
+    mix(&p->sx, sizeof(p->sx));
+    mix(&p->sy, sizeof(p->sy));
+    mix(&p->dens.family, sizeof(p->dens.family));
+    mix(&p->dens.coef_mode, sizeof(p->dens.coef_mode));
+    mix(p->dens.params, sizeof(p->dens.params));
+    mix(p->h_table.data(), p->h_table.size() * sizeof(double));
+    mix(p->h_edges.data(), p->h_edges.size() * sizeof(double));
+    mix(p->h_mask.data(), p->h_mask.size());
+    return h;
+}
+
+bool same_mc(const sdd_mc_params& a, const sdd_mc_params& b)
+{
+    return memcmp(&a, &b, sizeof(sdd_mc_params)) == 0;
+}
+}  // namespace
+
+int sdd_interface_mc_advance(sdd_plan* p, const sdd_mc_params* mc, uint64_t max_items,
+                             uint64_t* items_done, uint64_t* items_total, void* stream_)
+{
+    NvtxRange nvtx_range("sdd_interface_mc_advance");
+    clear_error();
+    if (!p || !mc) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = validate_mc(mc))) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    McArgs a;
+    bool few = false;
+    if ((rc = mc_args(p, mc, nullptr, nullptr, nullptr, a, few, stream))) return rc;
+    if (!p->resume_active || !same_mc(p->resume_mc, *mc)) {     // a new split run
+        p->resume_active = true;
+        p->resume_mc = *mc;
+        p->resume_next = 0;
+        p->resume_total = a.total_items;
+    }
+    const uint64_t end = std::min(p->resume_total, p->resume_next + max_items);
+    a.item_base = p->resume_next;
+    a.total_items = end;
+    if ((rc = launch_mc_paths(a, mc->precision,
+                              mesh_kernel_class(a.single.family, a.single.nb, a.single.stepper),
+                              stream)))
+        return rc;
+    p->resume_next = end;
+    p->last_stream = stream;
+    if (items_done) *items_done = p->resume_next;
+    if (items_total) *items_total = p->resume_total;
+    return SDD_OK;
+}
+
+int sdd_interface_mc_finish(sdd_plan* p, const sdd_mc_params* mc, double* mean, double* stderr_,
+                            sdd_mc_stats* stats, void* stream_)
+{
+    NvtxRange nvtx_range("sdd_interface_mc_finish");
+    clear_error();
+    if (!p || !mc) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_device(p);
+    if (rc) return rc;
+    if (!p->resume_active || !same_mc(p->resume_mc, *mc))
+        return fail(SDD_ERR_INVALID_ARG, "no split Monte Carlo run with these parameters");
+    if (p->resume_next != p->resume_total)
+        return fail(SDD_ERR_INVALID_ARG, "the split run has work items left: " +
+                                             std::to_string(p->resume_total - p->resume_next));
+    cudaStream_t stream = as_stream(stream_);
+    const bool mean_dev = is_device_ptr(mean), se_dev = is_device_ptr(stderr_);
+    McArgs a;
+    bool few = false;
+    if ((rc = mc_args(p, mc, mean_dev ? mean : nullptr, se_dev ? stderr_ : nullptr, nullptr, a,
+                      few, stream)))
+        return rc;
+    SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
+    if ((rc = launch_mc_reduce(a, stream))) return rc;
+    if ((rc = mc_tail(p, mc, few, mean_dev ? mean : nullptr, se_dev ? stderr_ : nullptr, stream)))
+        return rc;
+    p->resume_active = false;
+    const size_t bytes = (size_t)p->n_nodes * 2 * sizeof(double);
+    bool host = false;
+    if (mean && !mean_dev && bytes) {
+        SDD_CUDA(cudaMemcpyAsync(mean, p->d_mean, bytes, cudaMemcpyDeviceToHost, stream));
+        host = true;
+    }
+    if (stderr_ && !se_dev && bytes) {
+        SDD_CUDA(cudaMemcpyAsync(stderr_, p->d_stderr, bytes, cudaMemcpyDeviceToHost, stream));
+        host = true;
+    }
+    if (stats) return read_mc_stats(p, stats, stream);
+    if (host) SDD_CUDA(cudaStreamSynchronize(stream));
+    return SDD_OK;
+}
+
+int sdd_mc_checkpoint_bytes(const sdd_plan* p, uint64_t* bytes)
+{
+    clear_error();
+    if (!p || !bytes) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (!p->resume_active) return fail(SDD_ERR_INVALID_ARG, "no split Monte Carlo run to save");
+    *bytes = sizeof(CheckpointHeader) + p->resume_next * sizeof(Slot);
+    return SDD_OK;
+}
+
+int sdd_mc_checkpoint_save(sdd_plan* p, void* host, uint64_t bytes, void* stream_)
+{
+    NvtxRange nvtx_range("sdd_mc_checkpoint_save");
+    clear_error();
+    if (!p || !host) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (!p->resume_active) return fail(SDD_ERR_INVALID_ARG, "no split Monte Carlo run to save");
+    const uint64_t need = sizeof(CheckpointHeader) + p->resume_next * sizeof(Slot);
+    if (bytes < need)
+        return fail(SDD_ERR_INVALID_ARG, "checkpoint buffer too small: " + std::to_string(need) +
+                                             " bytes needed");
+    int rc = check_device(p);
+    if (rc) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    CheckpointHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kCheckpointMagic;
+    h.version = 1;
+    h.n = (uint64_t)p->n;
+    h.n_mc = (uint64_t)p->n_mc;
+    h.items_total = p->resume_total;
+    h.items_done = p->resume_next;
+    h.slot_bytes = sizeof(Slot);
+    h.plan_hash = plan_hash(p);
+    h.mc = p->resume_mc;
+    memcpy(host, &h, sizeof(h));
+    if (p->resume_next)
+        SDD_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(host) + sizeof(h), p->d_slots,
+                                 p->resume_next * sizeof(Slot), cudaMemcpyDeviceToHost, stream));
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    return SDD_OK;
+}
+
+int sdd_mc_checkpoint_load(sdd_plan* p, const void* host, uint64_t bytes, void* stream_)
+{
+    NvtxRange nvtx_range("sdd_mc_checkpoint_load");
+    clear_error();
+    if (!p || !host) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < sizeof(CheckpointHeader))
+        return fail(SDD_ERR_INVALID_ARG, "not a checkpoint (too short)");
+    CheckpointHeader h;
+    memcpy(&h, host, sizeof(h));
+    if (h.magic != kCheckpointMagic || h.version != 1 || h.slot_bytes != sizeof(Slot))
+        return fail(SDD_ERR_INVALID_ARG, "not a checkpoint of this library");
+    if (h.n != (uint64_t)p->n || h.n_mc != (uint64_t)p->n_mc || h.plan_hash != plan_hash(p))
+        return fail(SDD_ERR_INVALID_ARG, "the checkpoint belongs to another plan");
+    if (h.items_done > h.items_total ||
+        bytes < sizeof(CheckpointHeader) + h.items_done * sizeof(Slot))
+        return fail(SDD_ERR_INVALID_ARG, "checkpoint truncated");
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = validate_mc(&h.mc))) return rc;
+    cudaStream_t stream = as_stream(stream_);
+    McArgs a;
+    bool few = false;
+    if ((rc = mc_args(p, &h.mc, nullptr, nullptr, nullptr, a, few, stream))) return rc;
+    if (a.total_items != h.items_total)
+        return fail(SDD_ERR_INVALID_ARG, "the checkpoint's work-item count differs from the plan's");
+    if (h.items_done)
+        SDD_CUDA(cudaMemcpyAsync(p->d_slots, static_cast<const unsigned char*>(host) + sizeof(h),
+                                 h.items_done * sizeof(Slot), cudaMemcpyHostToDevice, stream));
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    p->resume_active = true;
+    p->resume_mc = h.mc;
+    p->resume_next = h.items_done;
+    p->resume_total = h.items_total;
+    p->last_stream = stream;
     return SDD_OK;
 }
 

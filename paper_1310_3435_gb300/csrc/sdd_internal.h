@@ -96,8 +96,9 @@ struct McArgs {
     int n_meshes;
     const uint64_t* item_off;
     const uint64_t* node_off;
-    uint64_t total_items;
+    uint64_t total_items;        // work items [item_base, total_items) are run
     uint64_t total_nodes;
+    uint64_t item_base;          // first work item of the launch (0 but in resumed runs)
     unsigned long long* queue;   // device work counter (reset by the launcher)
     Slot* slots;                 // total_items entries
     MeshDev single;
@@ -144,6 +145,12 @@ int launch_mc(const McArgs& args, int precision, int kc, cudaStream_t stream);
 // Same with a precomputed persistent-grid size (no device queries: usable
 // while a stream is being captured into a CUDA graph).
 int launch_mc_sized(const McArgs& args, int precision, int kc, int blocks, cudaStream_t stream);
+
+// The two halves of launch_mc, for runs split over several calls: the path
+// kernel over work items [item_base, total_items), and the per-node reduction
+// over every item of the run.
+int launch_mc_paths(const McArgs& args, int precision, int kc, cudaStream_t stream);
+int launch_mc_reduce(const McArgs& args, cudaStream_t stream);
 
 // Persistent-grid size of the path kernel for the current device.
 int mc_grid_blocks(int precision, int kc, bool one, int* blocks, int* threads);
@@ -244,6 +251,10 @@ struct sdd_plan {
     sdd::McStatsDev* d_stats = nullptr;
     uint64_t last_paths = 0;
     bool have_mc = false;
+    // a Monte Carlo run split over calls (sdd_interface_mc_advance / _finish)
+    bool resume_active = false;
+    sdd_mc_params resume_mc{};
+    uint64_t resume_next = 0, resume_total = 0;
     cudaEvent_t mc_done = nullptr;         // recorded after each single-plan Monte Carlo call
 
     // subdomain solves

@@ -166,12 +166,20 @@ def load(build_if_missing: bool = True):
     L.sdd_plan_placement.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.sdd_mesh_quality.argtypes = [vp, vp, vp, P(sdd_quality), vp]
     L.sdd_mesh_smooth.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+    u64p = P(ctypes.c_uint64)
+    L.sdd_interface_mc_advance.argtypes = [vp, P(sdd_mc_params), ctypes.c_uint64, u64p, u64p, vp]
+    L.sdd_interface_mc_finish.argtypes = [vp, P(sdd_mc_params), vp, vp, P(sdd_mc_stats), vp]
+    L.sdd_mc_checkpoint_bytes.argtypes = [vp, u64p]
+    L.sdd_mc_checkpoint_save.argtypes = [vp, vp, ctypes.c_uint64, vp]
+    L.sdd_mc_checkpoint_load.argtypes = [vp, vp, ctypes.c_uint64, vp]
     for name in ("sdd_mesh_plan", "sdd_plan_num_nodes", "sdd_plan_nodes", "sdd_plan_edges",
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
                  "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
                  "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
                  "sdd_batch_plan_stats", "sdd_interface_mc_static", "sdd_plan_set_placement",
-                 "sdd_plan_placement", "sdd_mesh_quality", "sdd_mesh_smooth"):
+                 "sdd_plan_placement", "sdd_mesh_quality", "sdd_mesh_smooth",
+                 "sdd_interface_mc_advance", "sdd_interface_mc_finish", "sdd_mc_checkpoint_bytes",
+                 "sdd_mc_checkpoint_save", "sdd_mc_checkpoint_load"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -420,6 +428,41 @@ def sdd_mesh_smooth(plan, mesh, steps: int, dt: float, k: float, stream=None) ->
     """Perona-Malik smoothing of `mesh` [n][n][2] in place (host or device)."""
     _check(load().sdd_mesh_smooth(plan, _ptr(mesh), int(steps), float(dt), float(k),
                                   _stream(stream)), "sdd_mesh_smooth")
+
+
+def sdd_interface_mc_advance(plan, mc: sdd_mc_params, max_items: int, stream=None):
+    """Runs the next work items of a split Monte Carlo run; returns
+    (items_done, items_total)."""
+    done, total = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().sdd_interface_mc_advance(plan, ctypes.byref(mc), int(max_items),
+                                           ctypes.byref(done), ctypes.byref(total),
+                                           _stream(stream)), "sdd_interface_mc_advance")
+    return int(done.value), int(total.value)
+
+
+def sdd_interface_mc_finish(plan, mc: sdd_mc_params, mean=None, stderr=None,
+                            want_stats: bool = True, stream=None):
+    st = sdd_mc_stats()
+    _check(load().sdd_interface_mc_finish(plan, ctypes.byref(mc), _ptr(mean), _ptr(stderr),
+                                          ctypes.byref(st) if want_stats else None,
+                                          _stream(stream)), "sdd_interface_mc_finish")
+    return st if want_stats else None
+
+
+def sdd_mc_checkpoint_save(plan, stream=None) -> bytes:
+    """The plan's split run as bytes (header + the sums of the items done)."""
+    n = ctypes.c_uint64()
+    _check(load().sdd_mc_checkpoint_bytes(plan, ctypes.byref(n)), "sdd_mc_checkpoint_bytes")
+    buf = ctypes.create_string_buffer(int(n.value))
+    _check(load().sdd_mc_checkpoint_save(plan, buf, n.value, _stream(stream)),
+           "sdd_mc_checkpoint_save")
+    return buf.raw
+
+
+def sdd_mc_checkpoint_load(plan, data: bytes, stream=None) -> None:
+    buf = ctypes.create_string_buffer(bytes(data), len(data))
+    _check(load().sdd_mc_checkpoint_load(plan, buf, len(data), _stream(stream)),
+           "sdd_mc_checkpoint_load")
 
 
 def sdd_plan_destroy(plan) -> None:
