@@ -221,8 +221,8 @@ struct RingF32 {
                                             float fdt = 1.0f) const
     {
         const float ds = s - cs, dtt = t - ct;
-        const float r2 = fmaf(ds, ds, dtt * dtt);
-        const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
+        const float r2 = fmaf(ds, ds, fmaf(dtt, dtt, 1e-30f));   // > 0 at the centre too
+        const float rinv = rsqrt_approx(r2);
         const float u = fmaf(r2, rinv, -r0);
         const float e = ex2_approx(c1 * fabsf(u));
         const float ope = 1.0f + e;
