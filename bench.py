@@ -36,9 +36,10 @@ import workloads as W  # noqa: E402
 # density, counted per thread:
 #   Philox4x32-10 / 2 steps: 10 rounds x (2 wide multiplies counted as 2,
 #   2 three-input xors, 2 key additions) = 60 -> 30 per step
-#   two uniforms (shift-or + add): 4;  Box-Muller pair: 10;  ring drift: 22;
-#   Euler-Maruyama update: 4;  exit test: 6;  step count and cap test: 2
-OPS_PER_STEP_RING_FP32 = 30 + 4 + 10 + 22 + 4 + 6 + 2        # = 78
+#   two uniforms (shift-or + add): 4;  Box-Muller pair: 9 (4 of them MUFU);
+#   ring drift: 21 (3 MUFU);  Euler-Maruyama update: 4;  exit test: 6;
+#   step count and cap test: 2
+OPS_PER_STEP_RING_FP32 = 30 + 4 + 9 + 21 + 4 + 6 + 2         # = 76
 # Exponential time stepping adds per step: a quarter of a Philox block for
 # the step lengths (15), one uniform (2), -log2 U with its clamp and the scale
 # by ln 2 (3), the length into the noise scale (1) and into the drift (1).
@@ -50,14 +51,14 @@ OPS_BRIDGE_EXTRA = 4.5
 OPS_BRIDGE_EXPO_EXTRA = 1.5
 
 
-# Drift evaluations other than the ring's 22: the tabulated density (cell
+# Drift evaluations other than the ring's 21: the tabulated density (cell
 # coordinates, clamps and weights 10, the cell index 2, one 16-byte read, the
 # two gradient components 2, the update 2) = 17.
-DRIFT_OPS = {W.FAMILY_RING: 22, W.FAMILY_TABLE: 17}
+DRIFT_OPS = {W.FAMILY_RING: 21, W.FAMILY_TABLE: 17}
 
 
 def ops_per_step(stepper: int, exit_test: int, family: int = W.FAMILY_RING) -> float:
-    ops = float(OPS_PER_STEP_RING_FP32) - DRIFT_OPS[W.FAMILY_RING] + DRIFT_OPS.get(family, 22)
+    ops = float(OPS_PER_STEP_RING_FP32) - DRIFT_OPS[W.FAMILY_RING] + DRIFT_OPS.get(family, 21)
     if stepper == W.STEP_EXPONENTIAL:
         ops += OPS_EXPO_EXTRA
     if exit_test == W.EXIT_BRIDGE:
