@@ -11,11 +11,16 @@
  *   - u(x) = E[boundary map at the first exit point of X]  (eq. ...StochasticSolutionA)
  *     for dX = grad(ln c) dt + sqrt(2) dW (eq. ...StochasticSolutionB, with the
  *     noise scale fixed by the expanded form, eq. ...Expanded);
- *   - Euler-Maruyama with time step dt and an exit test at the end of each
- *     step (§2.2); sample mean over N paths per node, error ~ N^-1/2 (§2.2);
+ *   - Euler-Maruyama with time step dt, or exponential time stepping of mean
+ *     step dt; an exit test at the end of each step, optionally with the
+ *     Brownian-bridge crossing probability (§2.2); sample mean over N paths
+ *     per node, error ~ N^-1/2 (§2.2);
  *   - interface values as Dirichlet data for independent subdomain solves,
  *     no iteration between subdomains (§2.1, Fig. 1; §3.5); conservative
- *     centred differences on a uniform grid (§3.2).
+ *     centred differences on a uniform grid (§3.2);
+ *   - around that path: few-point interfaces (§3.6), the fully probabilistic
+ *     mesh (§3.4), Perona-Malik smoothing (§3.5), mesh quality (§3.1, §3.3),
+ *     batches of meshes, runs split over calls with checkpoints.
  *
  * Conventions (all entry points):
  *   - Return SDD_OK (0) on success, a negative SDD_ERR_* code on failure;
