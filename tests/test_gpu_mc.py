@@ -227,3 +227,42 @@ def test_outputs_stay_inside_their_buffers(precision):
         assert torch.isnan(mean[m:]).all() and torch.isnan(se[m:]).all()
         assert (sums[m:] == -7).all()
         assert torch.isfinite(mesh[:n * n * 2]).all() and torch.isnan(mesh[n * n * 2:]).all()
+
+
+def test_ring_workload_at_full_size_matches_the_oracle_on_sampled_nodes(orc):
+    """The bench workload as the bench times it (257 x 257, 4 x 4, ring,
+    N = 1e5, dt = 1e-5, FP32 stepping, one single-mesh launch): two sampled
+    nodes, one on the ring's steep flank and one inside it, against the FP64
+    oracle on the same 1e5 Philox streams (run in path ranges over the host
+    cores).  The paired difference is the precision bias: within half a
+    standard error, and the step counts within 1e-3."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1310_3435_gb300 import native as N
+    spec = W.config2()
+    with gpu_plan(spec) as P:
+        g = N.sdd_interface_mc_sums(P.handle, P.mc_params())
+        nodes = P.nodes()
+    r = np.hypot(nodes[:, 0] / 256.0 - 0.5, nodes[:, 1] / 256.0 - 0.5)
+    pick = [int(np.argmin(np.abs(r - 0.27))), int(np.argmin(np.abs(r - 0.12)))]
+    E = orc.bmap_tables(spec.n, spec.bmap_mode, spec.family, spec.coef_mode, spec.params)
+    parts = 16
+    per = spec.paths // parts
+
+    def run(job):
+        k, q = job
+        return orc.mc_nodes(spec.n, nodes[[k]], E, spec.family, spec.coef_mode, spec.params,
+                            seed=spec.seed, paths=per, dt=spec.dt, max_steps=spec.cap(),
+                            tie_delta=spec.tie(), node_ids=[k], threads=1, path_begin=q * per)
+
+    jobs = [(k, q) for k in pick for q in range(parts)]
+    with ThreadPoolExecutor(max_workers=orc.default_threads()) as ex:
+        outs = list(ex.map(run, jobs))
+    for a, k in enumerate(pick):
+        mine = outs[a * parts:(a + 1) * parts]
+        S = sum(o["S_all"][0] for o in mine)
+        Q = sum(o["Q_all"][0] for o in mine)
+        steps = sum(int(o["steps"][0]) for o in mine)
+        mo, so = orc.mc_estimate(nodes[[k]], spec.n, S[None, :], Q[None, :], [spec.paths])
+        mg, _ = gpu_means(g[[k]], spec.n, nodes[[k]])
+        assert np.all(np.abs(mg - mo) <= 0.5 * so), (k, mg, mo, so)
+        assert abs(int(g["steps"][k]) - steps) / steps < 1e-3
