@@ -266,3 +266,35 @@ def test_ring_workload_at_full_size_matches_the_oracle_on_sampled_nodes(orc):
         mg, _ = gpu_means(g[[k]], spec.n, nodes[[k]])
         assert np.all(np.abs(mg - mo) <= 0.5 * so), (k, mg, mo, so)
         assert abs(int(g["steps"][k]) - steps) / steps < 1e-3
+
+
+def test_largest_grid_and_table(orc):
+    """The largest grid a plan takes (n = 16385, 2 x 2: 32765 interface nodes,
+    interface lines 8192 apart from the sides) with a few paths per node, and
+    the largest density table (4097 x 4097): counts and sampled nodes against
+    the oracle in FP64, and FP32 paired with FP64."""
+    from paper_1310_3435_gb300 import native as N
+    spec = W.MeshSpec(n=16385, sx=2, sy=2, family=W.FAMILY_RING,
+                      params=(10.0, 0.5, 0.5, 50.0, 0.25), paths=8, dt=1e-4, seed=2)
+    with gpu_plan(spec) as P:
+        assert P.n_nodes == 2 * 16383 - 1
+        g = N.sdd_interface_mc_sums(P.handle, P.mc_params())
+        g32 = N.sdd_interface_mc_sums(P.handle, P.mc_params(precision=W.FP32_STEP))
+        nodes = P.nodes()
+    assert np.all(g["paths"] == 8) and np.all(g32["paths"] == 8)
+    pick = np.linspace(0, len(nodes) - 1, 12).astype(int)
+    o = oracle_sums(orc, spec, nodes=nodes[pick], node_ids=pick)
+    _compare_fp64(orc, spec, g[pick], o, nodes[pick])
+    m64, se64 = gpu_means(g, spec.n, nodes)
+    m32, _ = gpu_means(g32, spec.n, nodes)
+    assert np.mean(np.abs(m32 - m64)) < 0.1 * np.mean(se64)
+
+    tn = 4097
+    table = W.table_params(W.smooth_field(tn, seed=5, amplitude=1.0, modes=3))
+    spec = W.MeshSpec(n=129, sx=2, sy=2, family=W.FAMILY_TABLE, params=table, paths=256,
+                      dt=1e-4, seed=3)
+    nodes = orc.interface_nodes(spec.n, spec.sx, spec.sy)
+    pick = np.arange(0, len(nodes), 25)
+    g = gpu_sums(spec)
+    o = oracle_sums(orc, spec, nodes=nodes[pick], node_ids=pick)
+    _compare_fp64(orc, spec, g[pick], o, nodes[pick])

@@ -83,11 +83,14 @@ def bumps(*bs) -> tuple:
     return tuple(out)
 
 
-def table_params(values) -> tuple:
-    """TABLE family parameters from a [tn, tn] array of ln w (row b = t index)."""
+def table_params(values) -> np.ndarray:
+    """TABLE family parameters from a [tn, tn] array of ln w (row b = t
+    index): a read-only flat array [tn, values...]."""
     v = np.asarray(values, dtype=np.float64)
     assert v.ndim == 2 and v.shape[0] == v.shape[1] and v.shape[0] >= 2
-    return (float(v.shape[0]),) + tuple(float(x) for x in v.ravel())
+    out = np.concatenate([[float(v.shape[0])], v.ravel()])
+    out.flags.writeable = False
+    return out
 
 
 def smooth_field(tn: int, seed: int = 0, amplitude: float = 1.0, modes: int = 4) -> np.ndarray:
