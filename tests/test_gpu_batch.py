@@ -113,3 +113,81 @@ def test_autotuned_parameters_are_valid_and_keep_results(tmp_path):
     # CG dot products are reduced over the CTA's threads: meshes agree to the
     # solve tolerance (relative residual 1e-10), not bit for bit
     assert np.max(np.abs(mesh - base[0])) < 1e-8, np.max(np.abs(mesh - base[0]))
+
+
+def test_uneven_batch_at_full_size_matches_the_oracle_on_sampled_nodes(orc):
+    """The batched workload as the bench times it (256 uneven meshes,
+    n in {65, 129, 257, 513}, splits 2..8, one bump each, N = 2e4 paths,
+    dt = 5e-5, FP32 stepping, one batch replayed as a CUDA graph; the bench's
+    autotuned chunk sizes leave the sums unchanged, they are exact): every
+    mesh's counts and solves, and two nodes of each of six meshes (one of
+    each grid size among them; one node next to the bump, one drawn at
+    random) against the FP64 oracle on the same 2e4 Philox streams.  The
+    paired difference is the precision bias: within half a standard error."""
+    from concurrent.futures import ThreadPoolExecutor
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    specs = W.config3()
+    assert len(specs) == 256 and {s.n for s in specs} == {65, 129, 257, 513}
+    plans = [gpu_plan(s) for s in specs]
+    means = []
+    try:
+        stream = torch.cuda.Stream()
+        with N.Batch(plans) as B:
+            B.run(use_graph=True, stream=stream)
+            stream.synchronize()
+            for i, (spec, P) in enumerate(zip(specs, plans)):
+                ms, ss = B.stats(i)
+                # every path scored; paths still inside at the step cap (2 / dt
+                # steps, scored at the nearest side) stay rare
+                assert ms.paths == spec.paths * P.n_nodes and ms.non_exits <= 1e-3 * ms.paths, i
+                assert ss.converged == ss.subdomains, i
+                mean = np.zeros((P.n_nodes, 2))
+                se = np.zeros((P.n_nodes, 2))
+                N.sdd_plan_results(P.handle, None, mean, se)
+                assert np.all(np.isfinite(mean)) and np.all((mean > 0) & (mean < 1)), i
+                means.append((mean, se, P.nodes()))
+    finally:
+        for P in plans:
+            P.close()
+
+    rng = np.random.default_rng(11)
+    picked = []
+    for n in (65, 129, 257, 513):
+        picked.append(next(i for i, s in enumerate(specs) if s.n == n))
+    picked += [int(i) for i in rng.choice([i for i in range(256) if i not in picked], 2,
+                                          replace=False)]
+    parts = 4
+    jobs = []
+    for i in picked:
+        spec = specs[i]
+        nodes = means[i][2]
+        cs, ct = spec.params[2], spec.params[3]     # bumps: (count, A, cs, ct, ks, kt)
+        near = int(np.argmin(np.hypot(nodes[:, 0] / (spec.n - 1.0) - cs,
+                                      nodes[:, 1] / (spec.n - 1.0) - ct)))
+        for k in (near, int(rng.integers(len(nodes)))):
+            jobs += [(i, k, q) for q in range(parts)]
+    edges = {i: orc.bmap_tables(specs[i].n, specs[i].bmap_mode, specs[i].family,
+                                specs[i].coef_mode, specs[i].params) for i in picked}
+
+    def run(job):
+        i, k, q = job
+        spec = specs[i]
+        per = spec.paths // parts
+        return orc.mc_nodes(spec.n, means[i][2][[k]], edges[i], spec.family, spec.coef_mode,
+                            spec.params, seed=spec.seed, paths=per, dt=spec.dt,
+                            max_steps=spec.cap(), tie_delta=spec.tie(), node_ids=[k],
+                            threads=1, path_begin=q * per)
+
+    with ThreadPoolExecutor(max_workers=orc.default_threads()) as ex:
+        outs = list(ex.map(run, jobs))
+    for a in range(0, len(jobs), parts):
+        i, k, _ = jobs[a]
+        spec = specs[i]
+        mine = outs[a:a + parts]
+        S = sum(o["S_all"][0] for o in mine)
+        Q = sum(o["Q_all"][0] for o in mine)
+        nodes = means[i][2][[k]]
+        mo, so = orc.mc_estimate(nodes, spec.n, S[None, :], Q[None, :], [spec.paths])
+        mg = means[i][0][[k]]
+        assert np.all(np.abs(mg - mo) <= 0.5 * so), (spec.label, k, mg, mo, so)
