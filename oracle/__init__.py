@@ -465,8 +465,13 @@ def perona_malik(U: np.ndarray, steps: int, dt: float, k: float) -> np.ndarray:
     and Malik's discrete scheme); boundary values stay fixed:
       u <- u + dt/h^2 sum_{nb in E,W,N,S} g(|u_nb - u| / h) (u_nb - u)."""
     U = np.array(U, dtype=np.float64, copy=True)
-    n = U.shape[0]
-    h = 1.0 / (n - 1)
+    return _perona_malik_spacing(U, steps, dt, k, 1.0 / (U.shape[0] - 1))
+
+
+def _perona_malik_spacing(U: np.ndarray, steps: int, dt: float, k: float, h: float) -> np.ndarray:
+    """The FTCS steps of `perona_malik` on a rectangular block of nodes
+    U[j, i, comp] with node spacing h; the block's ring stays fixed."""
+    U = np.array(U, dtype=np.float64, copy=True)
     r = dt / (h * h)
 
     def flux(d):
@@ -481,6 +486,41 @@ def perona_malik(U: np.ndarray, steps: int, dt: float, k: float) -> np.ndarray:
                                           + flux(u[2:, 1:-1] - mid) + flux(u[:-2, 1:-1] - mid))
         U = V
     return U
+
+
+def smoothing_lines(n: int, s: int, shifted: bool) -> list:
+    """Lines (grid indices, boundary included) that bound the blocks smoothed
+    separately along one axis (§3.5, §4): the boundary and the interface lines
+    of an s-way split; shifted, the midlines floor((a + b) / 2) of those
+    blocks [a, b] instead, so that each original interface lies inside a block
+    (the paper's second smoothing cycle over shifted subdomains)."""
+    X = [0] + interface_indices(n, s) + [n - 1]
+    if shifted:
+        X = [0] + [(X[a] + X[a + 1]) // 2 for a in range(len(X) - 1)] + [n - 1]
+    return sorted(set(X))
+
+
+def perona_malik_subdomains(U: np.ndarray, steps: int, dt: float, k: float, sx: int, sy: int,
+                            shifted: bool = False) -> np.ndarray:
+    """Perona-Malik smoothing applied on each subdomain separately (§3.5, §4):
+    every block between consecutive smoothing lines (`smoothing_lines`) is
+    smoothed as a mesh of its own by `perona_malik`, its ring (the boundary and
+    interface nodes around it) held fixed, with the spacing h of the whole
+    grid.  The blocks only share their rings, so they are independent."""
+    U = np.asarray(U, dtype=np.float64)
+    n = U.shape[0]
+    out = U.copy()
+    X = smoothing_lines(n, sx, shifted)
+    Y = smoothing_lines(n, sy, shifted)
+    for b in range(len(Y) - 1):
+        for a in range(len(X) - 1):
+            i0, i1, j0, j1 = X[a], X[a + 1], Y[b], Y[b + 1]
+            if i1 - i0 < 2 or j1 - j0 < 2:
+                continue                       # no interior node
+            block = U[j0:j1 + 1, i0:i1 + 1]
+            sm = _perona_malik_spacing(block, steps, dt, k, 1.0 / (n - 1))
+            out[j0 + 1:j1, i0 + 1:i1] = sm[1:-1, 1:-1]
+    return out
 
 
 # ------------------------------------------------------- mesh quality -----
