@@ -608,6 +608,25 @@ def five_ring_ln_rho(tn: int, alpha: float = 0.2, R: float = 30.0) -> np.ndarray
     return 0.5 * np.log1p(alpha * (ux * ux + uy * uy))
 
 
+def huang_sloan_ln_rho(tn: int, alpha: float = 0.7, R: float = 15.0) -> np.ndarray:
+    """ln of the Huang-Sloan monitor of §4 (eq. HuangSloanMonitorFunction): the
+    arc-length monitor rho = sqrt(1 + alpha |grad u|^2) of the boundary layer
+    u = (1 - exp(R (x - 1))) sin(pi y) on the unit square, at its tn x tn nodes
+    (row b = y = b / (tn - 1))."""
+    g = np.arange(tn) / (tn - 1.0)
+    x, y = np.meshgrid(g, g, indexing="xy")
+    e = np.exp(R * (x - 1.0))
+    ux = -R * e * np.sin(np.pi * y)
+    uy = np.pi * (1.0 - e) * np.cos(np.pi * y)
+    return 0.5 * np.log1p(alpha * (ux * ux + uy * uy))
+
+
+# The Mackenzie front of §4 (eq. MackenzieMonitorFunction, alpha = 10, R = 50):
+# rho = 1 / (1 + alpha exp(-R (y - 1/2 - sin(2 pi x) / 4)^2)), so the
+# generator's coefficient 1/rho is the RIDGE family with these parameters.
+MACKENZIE_RIDGE = (10.0, 50.0, 0.5, 0.25, 1.0)
+
+
 def run_paper_performance(args):
     """The paper's performance study (§5, Table 5) in its workload shape on one
     GB300: the five-ring arc-length monitor (tabulated on 1025 x 1025 nodes,
@@ -675,7 +694,11 @@ def run_quality(args):
         (dt = 1e-4, k = 1000, §3.5; the reference smoothed alike);
       * the 2 x 2 stochastic-deterministic mesh at lambda = 1 / quality-dt,
         N = 1e3, 1e4, 1e5, with every interface node, 7 equispaced points per
-        line, or the extrema placement (§3.5, §3.6)."""
+        line, or the extrema placement (§3.5, §3.6);
+      * §4's further examples on the same grid, 2 x 2 with every interface
+        node: the Huang-Sloan monitor, and the Mackenzie front in the shape of
+        Tables 3 and 4 with global, per-subdomain and shifted-subdomain
+        smoothing, each against its own single-domain mesh."""
     import torch
     from paper_1310_3435_gb300 import native as N
     torch.cuda.set_device(0)
@@ -724,13 +747,56 @@ def run_quality(args):
                 dd.append(row(P, mesh, ref, N=paths,
                               placement=["all", "7 equispaced", "extrema"][place],
                               mc_nodes=n_mc, path_steps=int(ms.path_steps)))
+    # §4's further examples, 2 x 2 with every interface node, each against its
+    # own single-domain mesh: the Huang-Sloan monitor (tabulated ln rho on
+    # 257^2 nodes, coefficient 1/rho) at N = 1e4, lambda = 1e3 and 1e4; the
+    # Mackenzie front (coefficient 1/rho = the ridge) in the shape of the
+    # paper's Tables 3 (N = 1e4, lambda = 1e3 .. 1e4) and 4 (lambda = 5e3, N =
+    # 1e3 .. 1e4), without smoothing, with 5 Perona-Malik steps (dt = 1e-4,
+    # k = 1000) on the whole mesh, on each subdomain, and on each subdomain and
+    # then on the shifted subdomains; the reference of the smoothed rows is the
+    # single-domain mesh smoothed on the whole square, as in the paper's tables
+    further = []
+    m, sdt, sk = 5, 1e-4, 1000.0
+    for name, fam, params, mode, runs in (
+            ("Huang-Sloan", W.FAMILY_TABLE, W.table_params(huang_sloan_ln_rho(257)), W.COEF_INV_W,
+             ((1e3, 10000), (1e4, 10000))),
+            ("Mackenzie", W.FAMILY_RIDGE, MACKENZIE_RIDGE, W.COEF_W,
+             tuple((lam, 10000) for lam in (1e3, 2e3, 5e3, 1e4)) +
+             tuple((5e3, paths) for paths in (1000, 2000, 5000)))):
+        ex = dict(base, family=fam, params=params, coef_mode=mode)
+        with N.Plan(W.MeshSpec(sx=1, sy=1, paths=2, dt=1e-3, **ex)) as P:
+            ref_ex = np.zeros((n, n, 2))
+            N.sdd_subdomain_solve(P.handle, np.zeros((0, 2)), P.solve_params(), ref_ex)
+            ref_sm = ref_ex.copy()
+            N.sdd_mesh_smooth(P.handle, ref_sm, m, sdt, sk)
+        for lam, paths in runs:
+            spec = W.MeshSpec(sx=2, sy=2, paths=paths, dt=1.0 / lam, **ex)
+            with N.Plan(spec) as P:
+                mesh = np.zeros((n, n, 2))
+                ms, _ = N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), mesh)
+                info = dict(monitor=name, N=paths, lam=lam, path_steps=int(ms.path_steps))
+                further.append(row(P, mesh, ref_ex, smoothing="none", **info))
+                if name != "Mackenzie":
+                    continue
+                g = mesh.copy()
+                N.sdd_mesh_smooth(P.handle, g, m, sdt, sk)
+                further.append(row(P, g, ref_sm, smoothing="global", **info))
+                sub = mesh.copy()
+                N.sdd_mesh_smooth_subdomains(P.handle, sub, m, sdt, sk, False)
+                further.append(row(P, sub, ref_sm, smoothing="subdomains", **info))
+                N.sdd_mesh_smooth_subdomains(P.handle, sub, m, sdt, sk, True)
+                further.append(row(P, sub, ref_sm, smoothing="subdomains, then shifted", **info))
     print(json.dumps({"metric": "mesh quality vs single-domain mesh",
                       "workload": "running example, 29x29, 1D boundary map, exponential steps "
                                   "with the boundary test",
                       "single_domain": {"q_max": q_ref["q_max"], "q_mean": q_ref["q_mean"]},
                       "fully_probabilistic": {"lambda": 1000, "smoothing": "dt=1e-4, k=1000",
                                               "rows": full},
-                      "dd_2x2": {"lambda": 1.0 / args.quality_dt, "rows": dd}}))
+                      "dd_2x2": {"lambda": 1.0 / args.quality_dt, "rows": dd},
+                      "further_examples_2x2": {"grid": "29x29, every interface node",
+                                               "smoothing": "%d steps, dt=%g, k=%g" % (m, sdt, sk),
+                                               "rows": further}}))
     return 0
 
 

@@ -350,6 +350,19 @@ int sdd_mesh_quality(sdd_plan* plan, const double* mesh, const double* ref, sdd_
  * FTCS step loses its maximum principle), OOM, CUDA. */
 int sdd_mesh_smooth(sdd_plan* plan, double* mesh, int steps, double dt, double k, void* stream);
 
+/* The same smoothing applied on each subdomain separately (§3.5, §4: local
+ * smoothing, parallel over the subdomains): every node of an interface line
+ * of the plan's split is held fixed like the boundary, so each subdomain is
+ * smoothed with its ring as Dirichlet data.  shifted = 1 smooths over the
+ * subdomains shifted by half a subdomain instead (the paper's second cycle,
+ * which puts the original interfaces inside subdomains): the held lines are
+ * the midlines floor((a + b) / 2) of the plan's blocks [a, b] between
+ * consecutive lines of 0, the interface lines and n - 1, per axis.  Same
+ * arguments, memory and stream rules and errors as sdd_mesh_smooth, plus
+ * INVALID_ARG for shifted outside {0, 1}. */
+int sdd_mesh_smooth_subdomains(sdd_plan* plan, double* mesh, int steps, double dt, double k,
+                               int shifted, void* stream);
+
 /* Copies the plan's last results: mesh [n][n][2] (after a solve), interface
  * means and standard errors [n_nodes][2] (after a Monte Carlo call or a batch
  * run).  Each pointer may be NULL, host or device memory. */

@@ -1412,10 +1412,11 @@ int sdd_mesh_quality(sdd_plan* p, const double* mesh, const double* ref, sdd_qua
     return SDD_OK;
 }
 
-int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, void* stream_)
+// Smoothing with the lines marked in `hold` (n bytes: bit 0 column, bit 1
+// row; empty: none) held fixed besides the boundary.
+static int smooth_mesh(sdd_plan* p, double* mesh, int steps, double dt, double k,
+                       const std::vector<uint8_t>& hold, void* stream_)
 {
-    NvtxRange nvtx_range("sdd_mesh_smooth");
-    clear_error();
     if (!p || !mesh) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     if (steps < 0) return fail(SDD_ERR_INVALID_ARG, "steps must be >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt) || !(k > 0.0) || !std::isfinite(k))
@@ -1438,7 +1439,20 @@ int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, v
     double* u = host ? tmp + count : mesh;
     if (host)
         SDD_CUDA(cudaMemcpyAsync(u, mesh, count * sizeof(double), cudaMemcpyHostToDevice, stream));
-    rc = launch_smooth(p->n, u, tmp, steps, dt, k, stream);
+    uint8_t* d_hold = nullptr;
+    if (!hold.empty()) {
+        {
+            AllocOn on(stream);
+            if ((rc = dev_alloc(&d_hold, hold.size()))) {
+                dev_free(tmp, stream);
+                return rc;
+            }
+        }
+        // pageable source: the copy has taken the bytes when the call returns
+        SDD_CUDA(cudaMemcpyAsync(d_hold, hold.data(), hold.size(), cudaMemcpyHostToDevice, stream));
+    }
+    rc = launch_smooth(p->n, u, tmp, steps, dt, k, d_hold, stream);
+    if (d_hold) dev_free(d_hold, stream);
     if (rc) {
         dev_free(tmp, stream);
         return rc;
@@ -1451,6 +1465,40 @@ int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, v
         dev_free(tmp, stream);
     }
     return SDD_OK;
+}
+
+int sdd_mesh_smooth(sdd_plan* p, double* mesh, int steps, double dt, double k, void* stream_)
+{
+    NvtxRange nvtx_range("sdd_mesh_smooth");
+    clear_error();
+    return smooth_mesh(p, mesh, steps, dt, k, {}, stream_);
+}
+
+// Lines bounding the blocks smoothed separately along one axis: the plan's
+// interface lines, or (shifted) the midlines floor((a + b) / 2) of the blocks
+// [a, b] between consecutive lines of 0, the interfaces and n - 1.
+static std::vector<int> smoothing_lines(int n, const std::vector<int>& iface, bool shifted)
+{
+    if (!shifted) return iface;
+    std::vector<int> X{0};
+    X.insert(X.end(), iface.begin(), iface.end());
+    X.push_back(n - 1);
+    std::vector<int> mid;
+    for (size_t a = 0; a + 1 < X.size(); ++a) mid.push_back((X[a] + X[a + 1]) / 2);
+    return mid;
+}
+
+int sdd_mesh_smooth_subdomains(sdd_plan* p, double* mesh, int steps, double dt, double k,
+                               int shifted, void* stream_)
+{
+    NvtxRange nvtx_range("sdd_mesh_smooth_subdomains");
+    clear_error();
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (shifted != 0 && shifted != 1) return fail(SDD_ERR_INVALID_ARG, "shifted must be 0 or 1");
+    std::vector<uint8_t> hold((size_t)p->n, 0);
+    for (int i : smoothing_lines(p->n, p->ix, shifted != 0)) hold[(size_t)i] |= 1u;
+    for (int j : smoothing_lines(p->n, p->iy, shifted != 0)) hold[(size_t)j] |= 2u;
+    return smooth_mesh(p, mesh, steps, dt, k, hold, stream_);
 }
 
 int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* mc,

@@ -135,8 +135,10 @@ int launch_quality(int n, int family, const double* params, const double* tab, i
 
 // Perona-Malik smoothing of the mesh u [n][n][2] (device), `steps` FTCS steps
 // ping-ponged with `scratch` (device, same size); the result ends in u.
+// hold: null, or n bytes (device) marking held columns (bit 0) and rows
+// (bit 1), whose nodes stay fixed like the boundary.
 int launch_smooth(int n, double* u, double* scratch, int steps, double dt, double k,
-                  cudaStream_t stream);
+                  const uint8_t* hold, cudaStream_t stream);
 
 // Launches the path kernel (for kernel class `kc`) and the per-node
 // reduction.

@@ -588,7 +588,10 @@ __global__ void __launch_bounds__(256) k_quality(QualityArgs a, const double2* _
 // u -> v per launch, both components: each of a node's four edges conducts
 // with g = exp(-(d/h)^2 / k^2) of its own difference d = u_nb - u, so
 //   v = u + r (g_E d_E + g_W d_W + g_N d_N + g_S d_S),  r = dt / h^2;
-// boundary nodes are copied.  One thread per node, mesh rows of double2.
+// boundary nodes are copied, and so are the nodes of held lines (hold[i]
+// bit 0: column i, hold[j] bit 1: row j; hold may be null): with the
+// subdomains' interface lines held, every subdomain is smoothed on its own
+// (§3.5, §4).  One thread per node, mesh rows of double2.
 __device__ __forceinline__ double pm_flux(double d, double h, double k2)
 {
     const double t = d / h;
@@ -597,13 +600,14 @@ __device__ __forceinline__ double pm_flux(double d, double h, double k2)
 
 __global__ void __launch_bounds__(256) k_pm_step(int n, const double2* __restrict__ u,
                                                  double2* __restrict__ v, double h, double r,
-                                                 double k2)
+                                                 double k2, const uint8_t* __restrict__ hold)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= (int64_t)n * n) return;
     const int i = (int)(g % n), j = (int)(g / n);
     const double2 c = u[g];
-    if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
+    if (i == 0 || j == 0 || i == n - 1 || j == n - 1 ||
+        (hold && ((hold[i] & 1u) | (hold[j] & 2u)))) {
         v[g] = c;
         return;
     }
@@ -638,7 +642,7 @@ int launch_quality(int n, int family, const double* params, const double* tab, i
 }
 
 int launch_smooth(int n, double* u, double* scratch, int steps, double dt, double k,
-                  cudaStream_t stream)
+                  const uint8_t* hold, cudaStream_t stream)
 {
     if (steps <= 0) return SDD_OK;
     const double h = 1.0 / (double)(n - 1);
@@ -648,7 +652,7 @@ int launch_smooth(int n, double* u, double* scratch, int steps, double dt, doubl
     double2* a = reinterpret_cast<double2*>(u);
     double2* b = reinterpret_cast<double2*>(scratch);
     for (int s = 0; s < steps; ++s) {
-        k_pm_step<<<blocks, 256, 0, stream>>>(n, a, b, h, r, k2);
+        k_pm_step<<<blocks, 256, 0, stream>>>(n, a, b, h, r, k2, hold);
         SDD_CUDA(cudaGetLastError());
         count_launch();
         std::swap(a, b);

@@ -166,6 +166,8 @@ def load(build_if_missing: bool = True):
     L.sdd_plan_placement.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.sdd_mesh_quality.argtypes = [vp, vp, vp, P(sdd_quality), vp]
     L.sdd_mesh_smooth.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+    L.sdd_mesh_smooth_subdomains.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, vp]
     u64p = P(ctypes.c_uint64)
     L.sdd_interface_mc_advance.argtypes = [vp, P(sdd_mc_params), ctypes.c_uint64, u64p, u64p, vp]
     L.sdd_interface_mc_finish.argtypes = [vp, P(sdd_mc_params), vp, vp, P(sdd_mc_stats), vp]
@@ -178,7 +180,7 @@ def load(build_if_missing: bool = True):
                  "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
                  "sdd_batch_plan_stats", "sdd_interface_mc_static", "sdd_plan_set_placement",
                  "sdd_plan_placement", "sdd_mesh_quality", "sdd_mesh_smooth",
-                 "sdd_interface_mc_advance", "sdd_interface_mc_finish", "sdd_mc_checkpoint_bytes",
+                 "sdd_mesh_smooth_subdomains", "sdd_interface_mc_advance", "sdd_interface_mc_finish", "sdd_mc_checkpoint_bytes",
                  "sdd_mc_checkpoint_save", "sdd_mc_checkpoint_load"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -428,6 +430,15 @@ def sdd_mesh_smooth(plan, mesh, steps: int, dt: float, k: float, stream=None) ->
     """Perona-Malik smoothing of `mesh` [n][n][2] in place (host or device)."""
     _check(load().sdd_mesh_smooth(plan, _ptr(mesh), int(steps), float(dt), float(k),
                                   _stream(stream)), "sdd_mesh_smooth")
+
+
+def sdd_mesh_smooth_subdomains(plan, mesh, steps: int, dt: float, k: float, shifted: bool = False,
+                               stream=None) -> None:
+    """Perona-Malik smoothing of `mesh` on each subdomain separately (interface
+    lines held), or on the subdomains shifted by half a subdomain."""
+    _check(load().sdd_mesh_smooth_subdomains(plan, _ptr(mesh), int(steps), float(dt), float(k),
+                                             1 if shifted else 0, _stream(stream)),
+           "sdd_mesh_smooth_subdomains")
 
 
 def sdd_interface_mc_advance(plan, mc: sdd_mc_params, max_items: int, stream=None):

@@ -79,3 +79,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 @pytest.mark.parametrize("steps,seconds", [(10, 2.0), (0, 1.0)])
 def test_achieved_rate(steps, seconds):
     assert bench.achieved_steps_per_s(steps, seconds) == pytest.approx(steps / seconds)
+
+
+def test_further_example_monitors():
+    """§4's monitors as the quality report feeds them: the Huang-Sloan ln rho
+    table against the printed formula at its nodes (row b is y = b/(tn-1)),
+    and the ridge parameters against the Mackenzie front's 1/rho."""
+    import math
+    tn = 9
+    L = bench.huang_sloan_ln_rho(tn)
+    assert L.shape == (tn, tn)
+    for a, b in ((0, 0), (8, 4), (6, 2), (3, 7)):
+        x, y = a / (tn - 1.0), b / (tn - 1.0)
+        e = math.exp(15.0 * (x - 1.0))
+        rho = math.sqrt(1.0 + 0.7 * (15.0 ** 2 * e ** 2 * math.sin(math.pi * y) ** 2 +
+                                     (1.0 - e) ** 2 * math.cos(math.pi * y) ** 2 * math.pi ** 2))
+        assert L[b, a] == pytest.approx(math.log(rho), rel=1e-13, abs=1e-15)
+    A, k, t0, amp, f = bench.MACKENZIE_RIDGE
+    for x, y in ((0.1, 0.6), (0.3, 0.75), (0.8, 0.25)):
+        ridge = 1.0 + A * math.exp(-k * (y - t0 - amp * math.sin(2 * math.pi * f * x)) ** 2)
+        rho = 1.0 / (1.0 + 10.0 * math.exp(-50.0 * (y - 0.5 - 0.25 * math.sin(2 * math.pi * x)) ** 2))
+        assert ridge == pytest.approx(1.0 / rho, rel=1e-14)

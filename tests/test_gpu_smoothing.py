@@ -43,6 +43,33 @@ def test_smoothing_matches_oracle(orc, steps, k):
     assert np.array_equal(host[0], U[0]) and np.array_equal(host[:, -1], U[:, -1])
 
 
+@pytest.mark.parametrize("sx,sy,shifted,steps", [(2, 2, False, 5), (3, 2, False, 1), (2, 3, True, 5),
+                                                  (4, 4, True, 2), (1, 1, True, 3), (5, 7, False, 10)])
+def test_subdomain_smoothing_matches_oracle(orc, sx, sy, shifted, steps):
+    """Smoothing on each subdomain (interface lines held) and on the shifted
+    subdomains, host and device meshes, against the oracle's block-by-block
+    smoothing; the held lines stay bitwise unchanged."""
+    import torch
+    from paper_1310_3435_gb300 import native as N
+    n, k = 29, 0.6
+    spec = W.MeshSpec(n=n, sx=sx, sy=sy, family=W.FAMILY_BUMPS,
+                      params=W.bumps((5.0, 0.5, 0.5, 50.0, 50.0)), paths=8, dt=1e-4, seed=1)
+    dt = 0.22 / (n - 1) ** 2
+    U = _noisy_mesh(n, seed=sx * 10 + sy)
+    want = orc.perona_malik_subdomains(U, steps, dt, k, sx, sy, shifted)
+    with gpu_plan(spec) as P:
+        host = U.copy()
+        N.sdd_mesh_smooth_subdomains(P.handle, host, steps, dt, k, shifted)
+        dev = torch.from_numpy(U.copy()).cuda()
+        N.sdd_mesh_smooth_subdomains(P.handle, dev, steps, dt, k, shifted)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), host)
+    assert np.max(np.abs(host - want)) < 1e-13
+    X = orc.smoothing_lines(n, sx, shifted)
+    Y = orc.smoothing_lines(n, sy, shifted)
+    assert np.array_equal(host[:, X], U[:, X]) and np.array_equal(host[Y, :], U[Y, :])
+
+
 def test_smoothing_validation():
     from paper_1310_3435_gb300 import native as N
     spec = W.small_parity_cases()[0]
@@ -58,6 +85,12 @@ def test_smoothing_validation():
             N.sdd_mesh_smooth(P.handle, U.copy(), -1, 1e-5, 1.0)
         with pytest.raises(N.SddError):
             N.sdd_mesh_smooth(P.handle, U.copy(), 1, 1e-5, 0.0)
+        with pytest.raises(N.SddError):
+            load = N.load()
+            rc = load.sdd_mesh_smooth_subdomains(P.handle, N._ptr(U.copy()), 1, 1e-5, 1.0, 2, None)
+            N._check(rc, "sdd_mesh_smooth_subdomains")
+        with pytest.raises(N.SddError):
+            N.sdd_mesh_smooth_subdomains(P.handle, U.copy(), 3, 0.3 / (n - 1) ** 2, 1.0, True)
 
 
 def test_fully_probabilistic_mesh_matches_oracle(orc):
