@@ -628,57 +628,135 @@ MACKENZIE_RIDGE = (10.0, 50.0, 0.5, 0.25, 1.0)
 
 
 def run_paper_performance(args):
-    """The paper's performance study (§5, Table 5) in its workload shape on one
-    GB300: the five-ring arc-length monitor (tabulated on 1025 x 1025 nodes,
-    w = 1/rho), 4 x 4 subdomains, n = 37 ... 197, N = 5000, exponential steps
-    with the boundary test at the paper's lambda = 1000 on [-1,1]^2 (mean step
-    1/(4 lambda) on the unit square), FP32 stepping; the Monte Carlo at every
-    interface node and at the extrema placement.  T_stoc and T_sub per mesh
-    are CUDA-event times after a warm-up, beside the paper's 16-core times."""
+    """The paper's performance study (§5) in its workload shape on one GB300:
+    the five-ring arc-length monitor (tabulated on 1025 x 1025 nodes, w =
+    1/rho), exponential steps with the boundary test at the paper's lambda =
+    1000 on [-1,1]^2 (mean step 1/(4 lambda) on the unit square), FP32
+    stepping, CG + FP64 refinement.  T_stoc and T_sub per mesh are CUDA-event
+    medians after a warm-up, beside the paper's 16-core times:
+      * Table 5: 4 x 4 subdomains, n = 37 ... 197, N = 5000, Monte Carlo at
+        every interface node and at the extrema placement;
+      * Tables 6 and 7: 157^2, 4 x 4, extrema placement, N = 500 ... 5000,
+        R against the single-domain mesh without and with smoothing on the
+        subdomains (5 steps, k = 1000, the largest stable FTCS step dt =
+        h^2 / 4: the paper's dt = 1e-4 is unstable on this grid; the paper
+        also smoothed the interface values with a third-party routine, which
+        is not reproduced);
+      * Table 8: 197^2, S = 2 x 2, 3 x 3, 4 x 4, extrema placement, N = 5000,
+        with T_1, the single-domain solve."""
     import torch
     from paper_1310_3435_gb300 import native as N
     torch.cuda.set_device(0)
     params = W.table_params(five_ring_ln_rho(1025))
-    paper = {37: (5.47, 0.00), 77: (7.56, 0.02), 117: (8.81, 0.08), 157: (8.88, 0.21),
-             197: (9.06, 0.47)}
     stream = torch.cuda.Stream()
+
+    def spec_of(n, s, paths):
+        return W.MeshSpec(n=n, sx=s, sy=s, family=W.FAMILY_TABLE, params=params,
+                          coef_mode=W.COEF_INV_W, bmap_mode=W.BMAP_PAPER_1D, paths=paths,
+                          dt=1.0 / 4000.0, precision=W.FP32_STEP, stepper=W.STEP_EXPONENTIAL,
+                          exit_test=W.EXIT_BRIDGE, solver=W.SOLVER_CG_FP32_REFINE, tol=1e-10)
+
+    def timed(P, place, reps=4, smooth_steps=0):
+        """Median T_stoc, T_sub (and T_smooth) over reps - 1 runs after a
+        warm-up; returns the times, the last mesh (host) and the MC stats."""
+        N.sdd_plan_set_placement(P.handle, place, 0)
+        mean = torch.zeros((P.n_nodes, 2), dtype=torch.float64, device="cuda")
+        mesh = torch.zeros((P.n, P.n, 2), dtype=torch.float64, device="cuda")
+        mc, sp = P.mc_params(), P.solve_params()
+        h = 1.0 / (P.n - 1)
+        t = {"mc": [], "sub": [], "smooth": []}
+        for rep in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            N.sdd_interface_mc(P.handle, mc, mean, None, want_stats=False, stream=stream)
+            e[1].record(stream)
+            N.sdd_subdomain_solve(P.handle, mean, sp, mesh, want_stats=False, stream=stream)
+            e[2].record(stream)
+            if smooth_steps:
+                N.sdd_mesh_smooth_subdomains(P.handle, mesh, smooth_steps, 0.25 * h * h, 1000.0,
+                                             False, stream=stream)
+            e[3].record(stream)
+            stream.synchronize()
+            if rep:                                   # the first run warms up
+                t["mc"].append(e[0].elapsed_time(e[1]) / 1000.0)
+                t["sub"].append(e[1].elapsed_time(e[2]) / 1000.0)
+                t["smooth"].append(e[2].elapsed_time(e[3]) / 1000.0)
+        st = N.sdd_plan_last_mc_stats(P.handle)
+        return ({k: float(np.median(v)) for k, v in t.items()}, mesh.cpu().numpy(), st)
+
+    def single_domain(n, reps=4):
+        """The single-domain mesh and its solve time T_1 (median after a warm-up)."""
+        with N.Plan(spec_of(n, 1, 2)) as P:
+            ref = torch.zeros((n, n, 2), dtype=torch.float64, device="cuda")
+            sp = P.solve_params()
+            ts = []
+            for rep in range(reps):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                e[0].record(stream)
+                N.sdd_subdomain_solve(P.handle, None, sp, ref, want_stats=False, stream=stream)
+                e[1].record(stream)
+                stream.synchronize()
+                if rep:
+                    ts.append(e[0].elapsed_time(e[1]) / 1000.0)
+            return ref.cpu().numpy(), float(np.median(ts))
+
+    def r_of(P, mesh, ref):
+        q = N.sdd_mesh_quality(P.handle, mesh, ref)
+        return {"R_max": q["r_max"], "R_mean": q["r_mean"], "folds": q["folds"]}
+
+    # Table 5
+    paper5 = {37: (5.47, 0.00), 77: (7.56, 0.02), 117: (8.81, 0.08), 157: (8.88, 0.21),
+              197: (9.06, 0.47)}
     rows = []
     for n in (37, 77, 117, 157, 197):
         for place in (N.SDD_PLACE_ALL, N.SDD_PLACE_EXTREMA):
-            spec = W.MeshSpec(n=n, sx=4, sy=4, family=W.FAMILY_TABLE, params=params,
-                              coef_mode=W.COEF_INV_W, bmap_mode=W.BMAP_PAPER_1D, paths=5000,
-                              dt=1.0 / 4000.0, precision=W.FP32_STEP, stepper=W.STEP_EXPONENTIAL,
-                              exit_test=W.EXIT_BRIDGE, solver=W.SOLVER_CG_FP32_REFINE, tol=1e-10)
-            with N.Plan(spec) as P:
-                N.sdd_plan_set_placement(P.handle, place, 0)
+            with N.Plan(spec_of(n, 4, 5000)) as P:
+                t, _, st = timed(P, place)
                 _, n_mc = N.sdd_plan_placement(P.handle)
-                mean = torch.zeros((P.n_nodes, 2), dtype=torch.float64, device="cuda")
-                mesh = torch.zeros((n, n, 2), dtype=torch.float64, device="cuda")
-                mc, sp = P.mc_params(), P.solve_params()
-                t_mc, t_sub = [], []
-                for rep in range(4):
-                    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                    e[0].record(stream)
-                    N.sdd_interface_mc(P.handle, mc, mean, None, want_stats=False, stream=stream)
-                    e[1].record(stream)
-                    N.sdd_subdomain_solve(P.handle, mean, sp, mesh, want_stats=False,
-                                          stream=stream)
-                    e[2].record(stream)
-                    stream.synchronize()
-                    if rep:                                   # the first run warms up
-                        t_mc.append(e[0].elapsed_time(e[1]) / 1000.0)
-                        t_sub.append(e[1].elapsed_time(e[2]) / 1000.0)
-                st = N.sdd_plan_last_mc_stats(P.handle)
             rows.append({"n": n, "placement": "all" if place == N.SDD_PLACE_ALL else "extrema",
                          "mc_nodes": n_mc, "path_steps": int(st.path_steps),
-                         "T_stoc_s": float(np.median(t_mc)), "T_sub_s": float(np.median(t_sub)),
-                         "paper_T_stoc_s": paper[n][0], "paper_T_sub_s": paper[n][1],
+                         "T_stoc_s": t["mc"], "T_sub_s": t["sub"],
+                         "paper_T_stoc_s": paper5[n][0], "paper_T_sub_s": paper5[n][1],
                          "non_exits": int(st.non_exits)})
-    print(json.dumps({"metric": "T_stoc, T_sub of the paper's performance study (Table 5 shape)",
-                      "workload": "five-ring arc-length monitor (table 1025^2), 4x4, N=5000, "
-                                  "exponential steps lambda=1000 on [-1,1]^2, boundary test, FP32",
-                      "paper_hardware": "16-core CPU machine (the paper's Table 5)",
-                      "rows": rows}))
+    # Tables 6 and 7
+    paper67 = {500: (0.04, 0.96, 0.46, 0.98, 0.91), 1000: (0.24, 0.98, 0.82, 0.99, 1.88),
+               2000: (0.71, 1.0, 0.96, 1.0, 3.68), 5000: (0.93, 1.0, 0.98, 1.0, 9.07)}
+    ref157, _ = single_domain(157)
+    rows67 = []
+    for paths in (500, 1000, 2000, 5000):
+        with N.Plan(spec_of(157, 4, paths)) as P:
+            t, mesh, st = timed(P, N.SDD_PLACE_EXTREMA, smooth_steps=5)
+            # the timed runs end smoothed: the same mesh once more without smoothing
+            plain = np.zeros_like(mesh)
+            N.sdd_mesh_generate(P.handle, P.mc_params(), P.solve_params(), plain)
+            r0 = r_of(P, plain, ref157)
+            r1 = r_of(P, mesh, ref157)
+        pr = paper67[paths]
+        rows67.append({"N": paths, "no_smoothing": r0, "subdomain_smoothing": r1,
+                       "T_stoc_s": t["mc"], "T_sub_s": t["sub"], "T_smooth_s": t["smooth"],
+                       "path_steps": int(st.path_steps),
+                       "paper": {"R_max": pr[0], "R_mean": pr[1], "R_max_smoothed": pr[2],
+                                 "R_mean_smoothed": pr[3], "T_stoc_s": pr[4], "T_sub_s": 0.21,
+                                 "T_smooth_s": 0.01}})
+    # Table 8
+    paper8 = {2: (0.96, 12.54, 14.89), 3: (0.89, 10.81, 2.95), 4: (0.96, 10.59, 0.46)}
+    ref197, t1 = single_domain(197)
+    rows8 = []
+    for s in (2, 3, 4):
+        with N.Plan(spec_of(197, s, 5000)) as P:
+            t, mesh, st = timed(P, N.SDD_PLACE_EXTREMA)
+            _, n_mc = N.sdd_plan_placement(P.handle)
+            r = r_of(P, mesh, ref197)
+        rows8.append({"S": s * s, "mc_nodes": n_mc, **r, "T_stoc_s": t["mc"], "T_sub_s": t["sub"],
+                      "T_total_s": t["mc"] + t["sub"], "T_1_s": t1,
+                      "paper": {"R_max": paper8[s][0], "T_stoc_s": paper8[s][1],
+                                "T_sub_s": paper8[s][2], "T_1_s": 64.0}})
+    print(json.dumps({"metric": "T_stoc, T_sub of the paper's performance study (Tables 5-8 shape)",
+                      "workload": "five-ring arc-length monitor (table 1025^2), N=5000 unless "
+                                  "stated, exponential steps lambda=1000 on [-1,1]^2, boundary "
+                                  "test, FP32",
+                      "paper_hardware": "16-core CPU machine (the paper's §5)",
+                      "rows": rows, "table6_7_157": rows67, "table8_197": rows8}))
     return 0
 
 
