@@ -19,7 +19,8 @@
  *     no iteration between subdomains (§2.1, Fig. 1; §3.5); conservative
  *     centred differences on a uniform grid (§3.2);
  *   - around that path: few-point interfaces (§3.6), the fully probabilistic
- *     mesh (§3.4), Perona-Malik smoothing (§3.5), mesh quality (§3.1, §3.3),
+ *     mesh (§3.4), Perona-Malik smoothing of the whole mesh or of each
+ *     subdomain (§3.5, §4), mesh quality (§3.1, §3.3),
  *     batches of meshes, runs split over calls with checkpoints.
  *
  * Conventions (all entry points):
