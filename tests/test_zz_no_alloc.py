@@ -29,13 +29,17 @@ def _inputs(spec):
     W.config1(paths=1000),                                               # FP64 stepping
     W.MeshSpec(n=41, sx=3, sy=2, family=W.FAMILY_RING, params=(10.0, 0.5, 0.5, 50.0, 0.25),
                paths=777, dt=1e-4, seed=9, precision=W.FP32_STEP),
+    W.MeshSpec(n=37, sx=2, sy=3, family=W.FAMILY_RIDGE, params=(20.0, 200.0, 0.3, 0.2, 1.0),
+               paths=640, dt=1e-4, seed=5, precision=W.FP32_STEP, stepper=W.STEP_EXPONENTIAL,
+               exit_test=W.EXIT_BRIDGE),                                 # the paper's stepper
 ])
 def test_static_scratch_matches_the_plan_entry_point_twice(spec):
     import torch
     from paper_1310_3435_gb300 import native as N
     nodes, edges, mean_ref, se_ref, dens = _inputs(spec)
     mc = N.mc_params(spec.paths, spec.dt, spec.seed, spec.precision, chunk=256,
-                     max_steps=spec.max_steps, tie_delta=spec.tie_delta)
+                     max_steps=spec.max_steps, tie_delta=spec.tie_delta,
+                     exit_test=spec.exit_test, stepper=spec.stepper)
     stream = torch.cuda.Stream()
     for _ in range(2):                               # the scratch keeps the last call's data
         mean = torch.full((nodes.shape[0], 2), -1.0, dtype=torch.float64, device="cuda")
