@@ -74,28 +74,49 @@ def env_rank():
 
 # DRAM bytes (read + write) of one launch of the path kernel at the 257 x 257
 # ring workload with constant steps and the end-of-step test, from one ncu
-# capture of the timed launch (dram__bytes_read.sum + dram__bytes_write.sum,
-# profiles/k_paths_fp32_ring257_launches.md).  Valid only for the kernel source
-# it was taken on: the bench line reports null traffic once the source's
-# SHA-256 differs.
+# capture of the timed launch (dram__bytes_read.sum + dram__bytes_write.sum).
+# Valid only for the kernel source it was taken on: the bench line reports
+# null traffic once the source's SHA-256 differs.
 PATH_KERNEL_TRAFFIC = {"bytes": 1104128 + 1055744,
                        "source_sha256": "4d2080faba5d65e441f327e48f3f4458f95dfcea13341faed31fc463c92d7dad"}
 
 
-def path_kernel_traffic(spec):
+# Pipe and issue activity of the same kernel from one `ncu --section
+# ComputeWorkloadAnalysis` capture (sm__inst_executed_pipe_fma / fmaheavy
+# cycles over elapsed cycles, and the issue-slot activity), keyed to the
+# kernel source like the traffic: null once the source changes.
+PATH_KERNEL_COUNTERS = {"fp32_fma_pipe": None, "issue_active": None, "source_sha256": ""}
+
+
+def _mc_source_digest():
     import hashlib
     src = os.path.join(ROOT, "paper_1310_3435_gb300", "csrc", "mc.cu")
     try:
         with open(src, "rb") as fh:
-            digest = hashlib.sha256(fh.read()).hexdigest()
+            return hashlib.sha256(fh.read()).hexdigest()
     except OSError:
         return None
-    default = (spec.n, spec.sx, spec.family, spec.paths, spec.dt, spec.stepper,
-               spec.exit_test) == (257, 4, W.FAMILY_RING, 100000, 1e-5, W.STEP_EULER,
-                                   W.EXIT_END_OF_STEP)
-    if default and digest == PATH_KERNEL_TRAFFIC["source_sha256"]:
+
+
+def _is_bench_workload(spec):
+    return (spec.n, spec.sx, spec.family, spec.paths, spec.dt, spec.stepper,
+            spec.exit_test) == (257, 4, W.FAMILY_RING, 100000, 1e-5, W.STEP_EULER,
+                                W.EXIT_END_OF_STEP)
+
+
+def path_kernel_traffic(spec):
+    if _is_bench_workload(spec) and _mc_source_digest() == PATH_KERNEL_TRAFFIC["source_sha256"]:
         return PATH_KERNEL_TRAFFIC["bytes"]
     return None
+
+
+def path_kernel_counters(spec):
+    """(FP32 FMA-pipe fraction, issue-slot fraction) of the recorded capture,
+    or (None, None) when it does not describe this workload and source."""
+    c = PATH_KERNEL_COUNTERS
+    if _is_bench_workload(spec) and _mc_source_digest() == c["source_sha256"]:
+        return c["fp32_fma_pipe"], c["issue_active"]
+    return None, None
 
 
 def measured_peaks():
@@ -232,7 +253,9 @@ def oracle_sample(spec, budget_s: float = 15.0, threads: int | None = None):
     return {"value": steps / el, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
             "sample": "%d of %d interface nodes x %d paths (FP64, %d path-steps, %.1f s)"
                       % (len(idx), len(nodes), paths, steps, el),
-            "seconds": el, "path_steps": steps}
+            "seconds": el, "path_steps": steps,
+            "_idx": idx, "_paths": paths, "_S": r["S_all"], "_Q": r["Q_all"],
+            "_steps": r["steps"], "_ties": r["ties"]}
 
 
 def run_reference(args):
@@ -391,20 +414,43 @@ def run_native(args):
                          "table" if spec.family == W.FAMILY_TABLE else "ring"),
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)"
                                    % (sms, sm_clock_max, peak_kind),
-                     "ops_per_path_step": ops},
+                     "ops_per_path_step": ops,
+                     "fp32_fma_pipe_frac_ncu": path_kernel_counters(spec)[0],
+                     "issue_frac_ncu": path_kernel_counters(spec)[1],
+                     "pipe_basis": "ncu of the timed kernel source: FMA-pipe cycles and issue "
+                                   "slots active over elapsed cycles; null if the source changed"},
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
     if e2e:
         line["e2e"] = e2e
+    line["mesh_quality"] = dict(mesh_quality_of(N, plan, mesh),
+                                note="the timed mesh: at N = 1e5 the interface std-err exceeds the "
+                                     "compressed spacing on the ring's flanks, so cells fold; the "
+                                     "workload measures throughput, not a usable mesh")
     if not args.no_fp64:
         line["fp64_gpu"] = fp64_leg(N, spec, stream, dev, args.fp64_paths)
         line["fp32_over_fp64"] = line["fp64_gpu"]["comparable_value"] and (
             achieved_steps_per_s(path_steps, t_mc) / line["fp64_gpu"]["comparable_value"])
+        line["fp64_gpu"]["equal_stderr"] = equal_stderr_leg(N, stream)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = {k: v for k, v in oracle_sample(spec, budget_s=args.ref_budget).items()
+        sample = oracle_sample(spec, budget_s=args.ref_budget)
+        line["cpu_baseline"] = {k: v for k, v in sample.items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}
+        line["precision_bias"] = precision_bias_leg(N, spec, sample, mc_stats.max_stderr, stream)
     plan.close()
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_leg(N, count=args.count)
+    if rank == 0 and not args.no_served:
+        line["served"] = serve_leg(args.served_rates, args.served_count, args.served_stderr,
+                                   1025, precision=W.FP32_STEP)
+        # plain FP64 against mixed precision on one smaller stream (FP64 stepping
+        # runs about 300x fewer path-steps/s): the same requests, both precisions
+        small = dict(rates=[args.fp64_served_rate], count=args.fp64_served_count,
+                     target_stderr=args.served_stderr, n_max=129)
+        line["served_fp64"] = {"fp64": serve_leg(precision=W.FP64, **small),
+                               "fp32_step_same_stream": serve_leg(precision=W.FP32_STEP, **small),
+                               "note": "scaled down to n <= 129 so that FP64 stepping keeps up"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -420,111 +466,28 @@ def run_batched(args):
     import torch
     from paper_1310_3435_gb300 import native as N
     torch.cuda.set_device(0)
-    specs = W.config3(count=args.count)
-    if args.paths:
-        specs = [W.MeshSpec(**{**sp.__dict__, "paths": args.paths}) for sp in specs]
-    plans = [N.Plan(sp) for sp in specs]
-    stream = torch.cuda.Stream()
-    tuned = None
-    t_tune = 0.0
-    mcs = [p.mc_params() for p in plans]
-    sps = [p.solve_params() for p in plans]
-    if not args.no_autotune:
-        from paper_1310_3435_gb300 import autotune
-        t0 = time.perf_counter()
-        tuner = autotune.Autotuner()
-        picks = [tuner.tune(sp, p.n_nodes) for sp, p in zip(specs, plans)]
-        tuner.save()
-        t_tune = time.perf_counter() - t0
-        mcs = [p.mc_params(chunk=k["chunk"]) for p, k in zip(plans, picks)]
-        sps = [p.solve_params(block_threads=k["block_threads"]) for p, k in zip(plans, picks)]
-        tuned = {"buckets_timed": tuner.timed, "seconds": t_tune,
-                 "block_threads": sorted({k["block_threads"] for k in picks}),
-                 "chunks": sorted({k["chunk"] for k in picks})}
-    t0 = time.perf_counter()
-    batch = N.Batch(plans, mcs, sps)
-    t_create = time.perf_counter() - t0
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        batch.run(use_graph=True, stream=stream)
-    stream.synchronize()
-    steps = 0
-    solve_ok = 0
-    for i in range(len(plans)):
-        ms, ss = batch.stats(i, allow_not_converged=True)
-        steps += int(ms.path_steps)
-        solve_ok += int(ss.converged == ss.subdomains)
-    sampler = ClockSampler(0)
-    launches0 = N.sdd_kernel_launches()
-    torch.cuda.synchronize()
-    sampler.start()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            evs[k][0].record(stream)
-            batch.run(use_graph=True, stream=stream)
-            evs[k][1].record(stream)
-            flush.zero_()
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms_steps = [a.elapsed_time(b) for a, b in evs]
-    t = sum(ms_steps) / 1000.0
-    nodes = sum(p.n_nodes for p in plans)
-    # phases timed apart (no graph): interface Monte Carlo, then fill + solves
-    ph = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    ph[0].record(stream)
-    batch.run_phases(1, stream=stream)
-    ph[1].record(stream)
-    batch.run_phases(2, stream=stream)
-    ph[2].record(stream)
-    torch.cuda.synchronize()
-    ms_mc, ms_solve = ph[0].elapsed_time(ph[1]), ph[1].elapsed_time(ph[2])
-    grid_nodes = sum(p.n * p.n for p in plans)
-    line = {"metric": "SDE path-steps/s", "value": steps * args.steps / t, "unit": "path-steps/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+    leg = batched_leg(N, count=args.count, paths=args.paths, autotune=not args.no_autotune,
+                      steps=args.steps, warmup=args.warmup)
+    line = {"metric": "SDE path-steps/s", "value": leg["path_steps_per_s"],
+            "unit": "path-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32-step/f64-acc", "data": "synthetic",
-            "config": {"workload": "batched uneven: %d meshes, n in {65,129,257,513}, splits 2..8, "
-                                   "1 bump, N=%d, dt=5e-5" % (len(plans), specs[0].paths),
-                       "interface_nodes": nodes, "path_steps_per_batch": steps,
-                       "l2": "flushed between timed steps", "graph": True},
-            "meshes_per_s": len(plans) * args.steps / t, "solves_converged": solve_ok,
-            "ms_interface_mc": ms_mc, "ms_fill_and_solves": ms_solve, "grid_nodes": grid_nodes,
-            "batch_create_s": t_create, "autotune": tuned, "clocks": clocks,
-            "gpu_launches": int(N.sdd_kernel_launches() - launches0)}
-    batch.close()
-    for p in plans:
-        p.close()
+            "config": {"workload": leg["workload"]}, "clocks": leg["clocks"],
+            "gpu_launches": leg["gpu_launches"], "batched": leg}
     print(json.dumps(line))
     return 0
 
 
 def run_serve(args):
     """Serving: Poisson stream of mesh requests (n log-uniform 65..n_max,
-    splits 2..8, 1-3 bumps), paths per node chosen by a pilot for std-err
-    <= 1e-3, continuous batching; p50/p99 latency and meshes/s."""
+    splits 2..8, 1-3 bumps), paths per node chosen by a pilot for the std-err
+    target, continuous batching; p50/p99 latency and meshes/s."""
     import torch
-    from paper_1310_3435_gb300 import serving as S
     torch.cuda.set_device(0)
-    out = []
-    for rate in args.rates:
-        arr = W.config5(count=args.count, rate=rate, seed=0, n_max=args.n_max)
-        reqs = [S.Request(i, a.spec, a.t) for i, a in enumerate(arr)]
-        srv = S.Server(hbm_budget=150e9, n_streams=3, max_batch=args.max_batch,
-                       target_stderr=args.target_stderr)
-        t0 = time.perf_counter()
-        res = srv.run(reqs)
-        wall = time.perf_counter() - t0
-        summ = S.summarize(res)
-        summ.update({"rate_req_s": rate, "wall_s": wall, "batches_launched": srv.launches,
-                     "peak_budget_bytes": srv.peak_used})
-        out.append(summ)
-    print(json.dumps({"metric": "served latency and meshes/s", "unit": "s",
-                      "workload": "Poisson stream, n log-uniform 65..%d, splits 2..8, 1-3 bumps, "
-                                  "std-err <= %g (pilot 1024 paths), dt=5e-5"
-                                  % (args.n_max, args.target_stderr),
-                      "requests_per_rate": args.count, "results": out}))
+    leg = serve_leg(args.rates, args.count, args.target_stderr, args.n_max,
+                    precision=W.FP32_STEP if args.precision is None else args.precision,
+                    max_batch=args.max_batch)
+    print(json.dumps(dict({"metric": "served latency and meshes/s", "unit": "s"}, **leg)))
     return 0
 
 
@@ -767,9 +730,9 @@ def run_quality(args):
     on the sides as boundary map, §3.2), with exponential time stepping and
     the boundary test as in the paper's experiments.  Against the
     single-domain mesh (Q_max, Q_mean, R_max, R_mean, l_inf; §3.1, §3.3):
-      * the fully probabilistic mesh (§3.4) at lambda = 1000, N = 1000 and
+      * the fully probabilistic mesh (§3.3) at lambda = 1000, N = 1000 and
         10000, and the N = 1000 mesh after m = 1, 2, 5, 10 Perona-Malik steps
-        (dt = 1e-4, k = 1000, §3.5; the reference smoothed alike);
+        (dt = 1e-4, k = 1000, §3.4; the reference smoothed alike);
       * the 2 x 2 stochastic-deterministic mesh at lambda = 1 / quality-dt,
         N = 1e3, 1e4, 1e5, with every interface node, 7 equispaced points per
         line, or the extrema placement (§3.5, §3.6);
@@ -906,6 +869,226 @@ def fp64_leg(N, spec, stream, dev, paths):
             "note": "interface Monte Carlo only, FP64 stepping"}
 
 
+# Algorithmic bytes of one multigrid-preconditioned FP32 CG iteration per
+# interior node of level 0 (float2 values of both components, FP32
+# coefficients): the operator product (read p and two edge coefficients per
+# node, write q: 8 + 8 + 8), the x and r updates (read p q x r, write x r:
+# 48), the red-black sweeps before and after the coarse correction (read r,
+# z, two coefficients, 1/diag, write z: 36 each, 72), the residual (read r z
+# and the coefficients, write t: 32), the restriction (read t: 8), the
+# prolongation (read and write z: 16), r.z (16) and the p update (read z p,
+# write p: 24).  The coarse levels add under a third of the V-cycle's bytes
+# and are not counted.
+SOLVE_BYTES_PER_NODE_ITERATION = 24 + 48 + 72 + 32 + 8 + 16 + 16 + 24     # = 240
+
+
+def precision_bias_leg(N, spec, sample, timed_max_stderr, stream):
+    """The precision-induced bias of the timed result, apart from its Monte
+    Carlo error: the GPU path in the timed precision on the cpu_baseline's
+    oracle sample (the same nodes and the same first paths, i.e. the same
+    Philox streams), paired with the FP64 oracle node by node."""
+    idx, paths = sample["_idx"], int(sample["_paths"])
+    sub = W.MeshSpec(**{**spec.__dict__, "paths": paths})
+    with N.Plan(sub) as P:
+        g = N.sdd_interface_mc_sums(P.handle, P.mc_params(precision=spec.precision), stream=stream)
+    S_o, Q_o = sample["_S"], sample["_Q"]
+    Nn = float(paths)
+    d = (g["sum"][idx] - S_o) / Nn                     # paired difference of the means
+    se_o = np.sqrt(np.maximum(Q_o - S_o ** 2 / Nn, 0.0) / (Nn * (Nn - 1.0)))
+    steps_o = int(np.asarray(sample["_steps"]).sum())
+    return {"sample": "%d nodes x first %d paths, the cpu_baseline's sample" % (len(idx), paths),
+            "max_abs": float(np.abs(d).max()), "mean_signed": float(d.mean()),
+            "max_abs_over_stderr": float((np.abs(d) / np.maximum(se_o, 1e-300)).max()),
+            "sample_stderr_max": float(se_o.max()),
+            "steps_rel_diff": abs(int(g["steps"][idx].sum()) - steps_o) / max(steps_o, 1),
+            "oracle_ties": int(np.asarray(sample["_ties"]).sum()),
+            "timed_result_max_stderr": float(timed_max_stderr),
+            "note": "GPU (timed precision) minus the FP64 oracle on identical streams: "
+                    "precision-induced bias; the timed result's Monte Carlo std-err beside it"}
+
+
+def mesh_quality_of(N, plan, mesh):
+    """Q_max, Q_mean and folded cells of a generated mesh (k_quality)."""
+    q = N.sdd_mesh_quality(plan.handle, mesh)
+    return {"q_max": q["q_max"], "q_mean": q["q_mean"], "folds": int(q["folds"])}
+
+
+def equal_stderr_leg(N, stream, reps=3):
+    """Plain FP64 against mixed precision at equal statistical accuracy: the
+    33 x 33, 2 x 2 bump workload at N = 4000, dt = 1e-4 (the same Philox
+    streams, so the same Monte Carlo error), one whole mesh generation each:
+    FP64 stepping + FP64 SOR, and FP32 stepping (FP64 sums) + FP32 CG with
+    FP64 refinement, both to 1e-10.  CUDA-event timed, median of `reps`
+    after a warm-up."""
+    import torch
+    spec = W.config1()
+    out = {"workload": spec.label + ", whole mesh generation", "reps": reps}
+    for name, prec, solver in (("fp64", W.FP64, W.SOLVER_SOR),
+                               ("fp32_step", W.FP32_STEP, W.SOLVER_CG_FP32_REFINE)):
+        with N.Plan(spec) as P:
+            mesh = torch.zeros((spec.n, spec.n, 2), dtype=torch.float64, device="cuda")
+            mc = P.mc_params(precision=prec)
+            sp = P.solve_params(solver=solver)
+            N.sdd_mesh_generate(P.handle, mc, sp, mesh, want_stats=False, stream=stream)
+            ms = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                N.sdd_mesh_generate(P.handle, mc, sp, mesh, want_stats=False, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            st = N.sdd_plan_last_mc_stats(P.handle)
+            t = float(np.median(ms)) / 1000.0
+            out[name] = {"meshes_per_s": 1.0 / t, "ms_per_mesh": 1000.0 * t,
+                         "path_steps_per_s": st.path_steps / t, "max_stderr": st.max_stderr,
+                         "solver": "SOR FP64" if solver == W.SOLVER_SOR else "CG FP32 + FP64 refinement"}
+    out["fp32_over_fp64_meshes_per_s"] = out["fp32_step"]["meshes_per_s"] / out["fp64"]["meshes_per_s"]
+    return out
+
+
+def batched_leg(N, count=256, paths=0, autotune=True, steps=1, warmup=1, stream=None):
+    """Batched uneven meshes (n in {65..513}, splits 2..8, one bump each,
+    N = 2e4, dt = 5e-5): one C-ABI batch, replayed as a CUDA graph, timed
+    with CUDA events (L2 flushed between timed runs); then the fill + solve
+    phase alone (from the interface values in place)."""
+    import torch
+    specs = W.config3(count=count)
+    if paths:
+        specs = [W.MeshSpec(**{**sp.__dict__, "paths": paths}) for sp in specs]
+    plans = [N.Plan(sp) for sp in specs]
+    stream = stream or torch.cuda.Stream()
+    tuned = None
+    mcs = [p.mc_params() for p in plans]
+    sps = [p.solve_params() for p in plans]
+    if autotune:
+        from paper_1310_3435_gb300 import autotune as AT
+        t0 = time.perf_counter()
+        tuner = AT.Autotuner()
+        picks = [tuner.tune(sp, p.n_nodes) for sp, p in zip(specs, plans)]
+        tuner.save()
+        mcs = [p.mc_params(chunk=k["chunk"]) for p, k in zip(plans, picks)]
+        sps = [p.solve_params(block_threads=k["block_threads"]) for p, k in zip(plans, picks)]
+        tuned = {"buckets_timed": tuner.timed, "seconds": time.perf_counter() - t0,
+                 "block_threads": sorted({k["block_threads"] for k in picks}),
+                 "chunks": sorted({k["chunk"] for k in picks})}
+    t0 = time.perf_counter()
+    batch = N.Batch(plans, mcs, sps)
+    t_create = time.perf_counter() - t0
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        batch.run(use_graph=True, stream=stream)
+    stream.synchronize()
+    launches0 = N.sdd_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            batch.run(use_graph=True, stream=stream)
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = N.sdd_kernel_launches() - launches0
+    t = sum(a.elapsed_time(b) for a, b in evs) / 1000.0
+    path_steps, solve_ok, max_se, max_iter = 0, 0, 0.0, 0
+    for i in range(len(plans)):
+        ms, ss = batch.stats(i, allow_not_converged=True)
+        path_steps += int(ms.path_steps)
+        solve_ok += int(ss.converged == ss.subdomains)
+        max_se = max(max_se, float(ms.max_stderr))
+        max_iter = max(max_iter, int(ss.max_iterations))
+
+    def solve_phase(b):
+        """The fill + solve phase alone, from the interface values in place."""
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            b.run_phases(2, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        work, its, ok = 0.0, 0, 0
+        for i in range(len(plans)):
+            _, ss = b.stats(i, allow_not_converged=True)
+            work += ss.node_iterations
+            its = max(its, int(ss.max_iterations))
+            ok += int(ss.converged == ss.subdomains)
+        return e0.elapsed_time(e1), work, its, ok
+
+    ms_solve, node_its, _, _ = solve_phase(batch)
+    # the same solves with the diagonal (Jacobi) preconditioner, for comparison
+    jac = N.Batch(plans, mcs, [p.solve_params(solver=W.SOLVER_CG_JACOBI_FP32_REFINE,
+                                              block_threads=sp.block_threads)
+                               for p, sp in zip(plans, sps)])
+    solve_phase(jac)                                  # warm-up
+    ms_jac, node_its_jac, its_jac, ok_jac = solve_phase(jac)
+    jac.close()
+    grid_nodes = sum(p.n * p.n for p in plans)
+    nodes = sum(p.n_nodes for p in plans)
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    solve_bytes = SOLVE_BYTES_PER_NODE_ITERATION * node_its
+    solve_gbs = solve_bytes / (ms_solve / 1000.0) / 1e9
+    out = {"workload": "batched uneven: %d meshes, n in {65,129,257,513}, splits 2..8, 1 bump, "
+                       "N=%d, dt=5e-5, one CUDA-graph replay per step" % (len(plans), specs[0].paths),
+           "interface_nodes": nodes, "grid_nodes": grid_nodes, "steps": steps, "warmup": warmup,
+           "path_steps_per_s": path_steps * steps / t, "meshes_per_s": len(plans) * steps / t,
+           "ms_per_step": 1000.0 * t / steps, "ms_fill_and_solves": ms_solve,
+           "ms_interface_mc": 1000.0 * t / steps - ms_solve,
+           "solve_roofline": {"bound": "hbm", "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
+                              "frac": solve_gbs / hbm, "node_iterations": node_its,
+                              "bytes_per_node_iteration": SOLVE_BYTES_PER_NODE_ITERATION,
+                              "peak_basis": "%s hbm_gbs" % peak_kind,
+                              "note": "multigrid-preconditioned FP32 CG: algorithmic bytes of "
+                                      "level 0 per interior node and iteration x the nodes and "
+                                      "iterations the solves ran, over the fill + solve phase"},
+           "jacobi_pcg": {"ms_fill_and_solves": ms_jac, "solve_max_iterations": its_jac,
+                          "node_iterations": node_its_jac, "solves_converged": ok_jac,
+                          "note": "the same solves with the diagonal preconditioner"},
+           "max_stderr": max_se, "solves_converged": solve_ok, "solve_max_iterations": max_iter,
+           "path_steps_per_batch": path_steps, "batch_create_s": t_create, "autotune": tuned,
+           "gpu_launches": int(launches), "clocks": clocks,
+           "l2": "flushed before each timed run"}
+    batch.close()
+    for p in plans:
+        p.close()
+    return out
+
+
+def serve_leg(rates, count, target_stderr, n_max, precision=W.FP32_STEP, max_batch=64,
+              reuse_pilot=True, seed=0):
+    """Serving runs: a Poisson stream of `count` mesh requests per rate (n
+    log-uniform 65..n_max, splits 2..8, 1-3 bumps, dt = 5e-5), paths per node
+    from a 1024-path pilot for the std-err target, continuous batching;
+    p50/p99 latency and meshes/s per rate."""
+    import torch
+    from paper_1310_3435_gb300 import serving as S
+    out = []
+    for rate in rates:
+        arr = W.config5(count=count, rate=rate, seed=seed, n_max=n_max)
+        reqs = [S.Request(i, W.MeshSpec(**{**a.spec.__dict__, "precision": precision}), a.t)
+                for i, a in enumerate(arr)]
+        srv = S.Server(hbm_budget=150e9, n_streams=3, max_batch=max_batch,
+                       target_stderr=target_stderr, reuse_pilot=reuse_pilot)
+        t0 = time.perf_counter()
+        res = srv.run(reqs)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        summ = S.summarize(res)
+        summ.update({"rate_req_s": rate, "wall_s": wall, "batches_launched": srv.launches,
+                     "peak_budget_bytes": srv.peak_used})
+        out.append(summ)
+    return {"workload": "Poisson stream, n log-uniform 65..%d, splits 2..8, 1-3 bumps, dt=5e-5, "
+                        "std-err target %g (paths per node from a 1024-path pilot%s), %s stepping"
+                        % (n_max, target_stderr, ", continued by the final run" if reuse_pilot else "",
+                           "FP32" if precision == W.FP32_STEP else "FP64"),
+            "requests_per_rate": count, "rates": out}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -945,6 +1128,15 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-paths", type=int, default=2048,
                     help="paths per node of the plain-FP64 GPU comparison leg")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave the batched (256 uneven meshes) leg out of the line")
+    ap.add_argument("--no-served", action="store_true",
+                    help="leave the served legs out of the line")
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[4.0, 16.0])
+    ap.add_argument("--served-count", type=int, default=200)
+    ap.add_argument("--served-stderr", type=float, default=5e-3)
+    ap.add_argument("--fp64-served-rate", type=float, default=0.5)
+    ap.add_argument("--fp64-served-count", type=int, default=24)
     ap.add_argument("--chunk", type=int, default=0, help="paths per work item (0: automatic)")
     ap.add_argument("--paths", type=int, default=0,
                     help="override paths per node (profiling runs on a small case)")

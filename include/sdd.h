@@ -19,7 +19,7 @@
  *     no iteration between subdomains (§2.1, Fig. 1; §3.5); conservative
  *     centred differences on a uniform grid (§3.2);
  *   - around that path: few-point interfaces (§3.6), the fully probabilistic
- *     mesh (§3.4), Perona-Malik smoothing of the whole mesh or of each
+ *     mesh (§3.3), Perona-Malik smoothing of the whole mesh (§3.4) or of each
  *     subdomain (§3.5, §4), mesh quality (§3.1, §3.3),
  *     batches of meshes, runs split over calls with checkpoints.
  *
@@ -59,6 +59,10 @@ extern "C" {
 #define SDD_ERR_CUDA          (-3)
 #define SDD_ERR_NOT_CONVERGED (-4)
 #define SDD_ERR_NO_DEVICE     (-5)
+/* There is no status code for a path stopped by the step cap: such paths are
+ * scored at their nearest side and counted (sdd_mc_stats.non_exits).  Time
+ * limits and cancellation belong to the caller's request loop (the Python
+ * server cancels a request between launches), not to a call of this ABI. */
 
 /* ---- density families (shapes of the paper's monitor functions) ---- */
 /* BUMPS: params = [nb, (A, cs, ct, ks, kt) x nb], nb <= 6:
@@ -139,9 +143,19 @@ extern "C" {
 #define SDD_PLACE_EQUISPACED 1
 #define SDD_PLACE_EXTREMA    2
 
-/* subdomain solvers */
-#define SDD_SOLVER_SOR            0   /* FP64 red-black SOR */
-#define SDD_SOLVER_CG_FP32_REFINE 1   /* FP32 Jacobi-PCG inner solves + FP64 iterative refinement */
+/* subdomain solvers (each to the relative residual tol of the FP64 system)
+ *   SOR                   : FP64 red-black SOR
+ *   CG_FP32_REFINE        : FP64 iterative refinement around FP32 conjugate
+ *                           gradients preconditioned by one geometric multigrid
+ *                           V-cycle (bilinear transfers, Galerkin coarse
+ *                           operators, Gauss-Seidel smoothing); tens of
+ *                           iterations where diagonal preconditioning takes
+ *                           hundreds to thousands
+ *   CG_JACOBI_FP32_REFINE : the same refinement around diagonally
+ *                           (Jacobi) preconditioned FP32 CG */
+#define SDD_SOLVER_SOR                   0
+#define SDD_SOLVER_CG_FP32_REFINE        1
+#define SDD_SOLVER_CG_JACOBI_FP32_REFINE 2
 
 typedef struct sdd_plan sdd_plan;
 
@@ -172,7 +186,27 @@ typedef struct {
     double tie_delta;                  /* <0: default (1e-11 FP64, 0 FP32) */
     int32_t exit_test;                 /* SDD_EXIT_END_OF_STEP | SDD_EXIT_BRIDGE */
     int32_t stepper;                   /* SDD_STEP_EULER | SDD_STEP_EXPONENTIAL */
+    int32_t reserved;                  /* 0 */
+    uint64_t path_begin;               /* 0: run every path.  > 0: continue the plan's
+                                          previous run (see below) */
 } sdd_mc_params;
+
+/* Continuing a run (mc->path_begin > 0).  The estimator is a sum over paths,
+ * so it is additive (§2.2; §6 notes the additivity of the expectation): a
+ * short run made first, e.g. a pilot that measures the standard error to
+ * choose N, need not be thrown away.  With path_begin = P the call takes
+ * paths [0, P) of every node from the work items of the plan's previous
+ * whole single-plan run (sdd_interface_mc, _sums or sdd_mesh_generate on this
+ * plan, whose items stay in the plan's buffer) and runs only paths [P, N).
+ * That run must have had paths_per_node = P and the same seed, dt,
+ * precision, chunk, effective step cap, tie delta, exit test and stepper; P
+ * must be a multiple of chunk, which must be given (not 0), and P <= N.  The
+ * result (means, errors, sums, statistics) is bitwise that of one run of N
+ * paths with the same chunk.  Batches accept it per plan (sdd_batch_create
+ * checks it; the plan's previous run must stay its last single-plan run
+ * until the batch has run).  Split runs (sdd_interface_mc_advance) and the
+ * allocation-free entry point take path_begin = 0 only.  Errors:
+ * INVALID_ARG when any condition above fails. */
 
 typedef struct {
     uint64_t paths;                    /* paths run, all nodes */
@@ -211,13 +245,15 @@ typedef struct {
     int32_t max_iterations;            /* largest iteration count over subdomains */
     int32_t reserved;
     double max_rel_residual;           /* largest final relative residual */
+    double node_iterations;            /* sum over subdomains of interior nodes x
+                                          iterations (the solves' work) */
 } sdd_solve_stats;
 
 /* Builds a plan for an n x n grid split sx x sy (2 <= ... see below) with
  * density `dens` and boundary map `bmap`: enumerates the interface nodes,
  * builds the boundary tables and copies them to the current device.
  * Requires 3 <= n <= 16385, 1 <= sx, sy <= n-1.  *out receives the plan.
- * sx = sy = n-1 gives the fully probabilistic mesh (§3.4): every interior
+ * sx = sy = n-1 gives the fully probabilistic mesh (§3.3): every interior
  * grid line is an interface, so every interior node is a Monte Carlo node
  * ((n-2)^2 of them) and every subdomain is one empty cell.
  * Errors: INVALID_ARG (sizes, unknown family/mode, nb > SDD_MAX_BUMPS, NULL),
@@ -300,9 +336,12 @@ int sdd_plan_last_mc_stats(sdd_plan* plan, sdd_mc_stats* stats);
 int sdd_subdomain_solve(sdd_plan* plan, const double* iface, const sdd_solve_params* sp,
                         double* mesh, sdd_solve_stats* stats, void* stream);
 
-/* Interface Monte Carlo followed by the subdomain solves, all on `stream`
- * with the interface values kept on the device.  Outputs (each may be NULL
- * except mesh): mesh [n][n][2], iface_mean / iface_stderr [n_nodes][2]. */
+/* The whole stochastic-deterministic decomposition (§2.1, Fig. 1): interface
+ * Monte Carlo followed by the subdomain solves, once, with no iteration
+ * between subdomains, all on `stream` with the interface values kept on the
+ * device.  Outputs (each may be NULL except mesh): mesh [n][n][2],
+ * iface_mean / iface_stderr [n_nodes][2].  Errors: those of
+ * sdd_interface_mc and sdd_subdomain_solve. */
 int sdd_mesh_generate(sdd_plan* plan, const sdd_mc_params* mc, const sdd_solve_params* sp,
                       double* mesh, double* iface_mean, double* iface_stderr,
                       sdd_mc_stats* mc_stats, sdd_solve_stats* solve_stats, void* stream);
@@ -338,7 +377,7 @@ typedef struct {
 int sdd_mesh_quality(sdd_plan* plan, const double* mesh, const double* ref, sdd_quality* out,
                      void* stream);
 
-/* Anisotropic (Perona-Malik) smoothing of a mesh (§3.5, eq.
+/* Anisotropic (Perona-Malik) smoothing of a mesh (§3.4, eq.
  * PeronaMalikDiffusion): `steps` forward-Euler, centred-in-space (FTCS) steps
  * of length dt of u_t = div(g grad u) for each component, g =
  * exp(-|grad u|^2 / k^2).  Each of a node's four edges conducts with g of its
@@ -412,24 +451,40 @@ void sdd_batch_destroy(sdd_batch* batch);
  * sums) is one file-scope 8 MiB device array inside the library, which every
  * GPU that loads the library keeps until the process exits.  It calls no
  * cudaMalloc, cudaFree or allocating routine.
- * Inputs, all device memory owned by the caller: nodes int32 [n_nodes][2]
- * (i, j), in the order whose index is the node's Philox counter word (the
- * plans' order reproduces sdd_interface_mc); edges, the boundary tables
- * [2][4][n].  Host inputs: dens, mc (as sdd_interface_mc).  Outputs, device
- * memory: mean [n_nodes][2] (required), stderr_ [n_nodes][2] (may be NULL).
- * Asynchronous on `stream`.
+ * Inputs, all device memory of the current device owned by the caller: nodes
+ * int32 [n_nodes][2] (i, j), in the order whose index is the node's Philox
+ * counter word (the plans' order reproduces sdd_interface_mc); edges, the
+ * boundary tables [2][4][n].  Host inputs: dens, mc (as sdd_interface_mc).
+ * Outputs, device memory: mean [n_nodes][2] (required), stderr_
+ * [n_nodes][2] (may be NULL).  Asynchronous on `stream`.
+ * Before any launch each buffer is checked: device (or managed) memory of
+ * the current device, 8-byte aligned, and an allocation that holds the
+ * bytes above from the pointer on (cuMemGetAddressRange); INVALID_ARG with a
+ * message otherwise.  Nodes must be interior, 0 < i, j < n-1: the kernel
+ * does not check them, and the estimate of a node outside that range is
+ * undefined (but reads and writes stay inside the buffers).
  * Limit: n_nodes * ceil(N / chunk) work items must fit the array (55185);
  * chunk = 0 picks the automatic size, raised up to 8192 until they fit;
  * larger requests fail with SDD_ERR_INVALID_ARG and a message.  The TABLE
  * density family is not accepted here (its table reaches the device through
- * a plan); INVALID_ARG.
- * The first call on a device looks the array's address up
+ * a plan); INVALID_ARG.  mc->path_begin must be 0.
+ * The first call on a device (and the first after that device's context was
+ * replaced, e.g. by cudaDeviceReset) looks the array's address up
  * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+ * share the array, which keeps the last call's contents (the parts that must
+ * start at zero are cleared by each call): calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller. */
 int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_nodes, const double* edges,
                             const sdd_density* dens, const sdd_mc_params* mc, double* mean,
                             double* stderr_, void* stream);
+
+/* Statistics (paths, path-steps, ties, capped paths, largest std-err) of the
+ * last sdd_interface_mc_static call on the current device, read from the head
+ * of its static array: synchronises `stream`, which must be the stream of
+ * that call or one ordered after it.  Errors: INVALID_ARG (no call yet),
+ * CUDA. */
+int sdd_interface_mc_static_stats(sdd_mc_stats* stats, void* stream);
 
 /* Frees the plan and its device buffers.  Memory is stream-ordered: the free
  * is queued on the plan's last stream after its work, and the call does not

@@ -23,7 +23,7 @@ Parts (each follows the passage it cites):
   with c at edge midpoints; subdomains take the interface values as Dirichlet
   data (§2.1, §3.5).  The linear solve is scipy's sparse direct solver.
 * ``closed_form_1d`` and ``torsion_exit_time``: the exact solutions used as pins.
-* ``perona_malik``: FTCS anisotropic smoothing of a mesh (§3.5).
+* ``perona_malik``: FTCS anisotropic smoothing of a mesh (§3.4).
 * ``cell_quality`` / ``mesh_quality``: Q(K), R_max, R_mean, l_inf (§3.1, §3.3);
   ``placement`` / ``interpolate_interface``: few-point interfaces (§3.6).
 """
@@ -457,7 +457,7 @@ def torsion_exit_time(s: float, t: float, terms: int = 401) -> float:
 
 # ---------------------------------------------------- mesh smoothing -----
 def perona_malik(U: np.ndarray, steps: int, dt: float, k: float) -> np.ndarray:
-    """Anisotropic (Perona-Malik) smoothing of a mesh U[j, i, comp] (§3.5,
+    """Anisotropic (Perona-Malik) smoothing of a mesh U[j, i, comp] (§3.4,
     eq. PeronaMalikDiffusion): `steps` forward-Euler, centred-in-space (FTCS)
     steps of length dt of u_t = div(g grad u) for each component separately,
     g = exp(-|grad u|^2 / k^2).  The conductance of each of a node's four

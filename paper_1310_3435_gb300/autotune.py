@@ -54,7 +54,9 @@ def largest_subdomain(spec) -> int:
 
 
 def solve_bucket(spec) -> str:
-    return "solve/s%d/m%d" % (spec.solver, int(math.log2(max(1, largest_subdomain(spec)))))
+    # "mg": the CG solver is multigrid-preconditioned (timings of the former
+    # diagonal preconditioner do not carry over)
+    return "solve/mg/s%d/m%d" % (spec.solver, int(math.log2(max(1, largest_subdomain(spec)))))
 
 
 class Autotuner:

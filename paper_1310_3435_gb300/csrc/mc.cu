@@ -878,6 +878,10 @@ __device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs
                 held = it;
                 held_valid = true;
             }
+            if ((uint32_t)((held - M.item_begin) % cpn) < M.chunk_begin) {
+                held_valid = false;                    // summed by the run this one continues
+                continue;
+            }
             const unsigned freeb = ~used & ((1u << N_SETS) - 1u);
             if (!freeb) break;                         // all sets busy: wait for a flush
             const int s = __ffs(freeb) - 1;
@@ -1234,6 +1238,7 @@ k_paths(const __grid_constant__ McArgs a)
             const uint64_t local = item - M.item_begin;
             const uint32_t node = (uint32_t)(local / M.chunks_per_node);
             const uint32_t chunk = (uint32_t)(local % M.chunks_per_node);
+            if (chunk < M.chunk_begin) continue;       // summed by the run this one continues
             Slot* out = a.slots + item;
             if constexpr (ONE) {
                 const ParamKeys keys{a.rk};

@@ -1,5 +1,6 @@
 // C ABI of libsdd.so: plans, interface Monte Carlo, subdomain solves and the
 // combined mesh generation (Bihlo & Haynes, §2.1-2.2, §3.2, §3.5).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -108,6 +109,11 @@ void dev_free(T*& p, cudaStream_t s)
 {
     if (p) cudaFreeAsync(p, s);
     p = nullptr;
+}
+
+int64_t interior_nodes(const SubDev& d)
+{
+    return (int64_t)std::max(d.i1 - d.i0 - 1, 0) * std::max(d.j1 - d.j0 - 1, 0);
 }
 
 // Subdomains in decreasing interior size: one CTA each, the largest (the
@@ -250,7 +256,8 @@ int alloc_solve_buffers(sdd_plan* p, cudaStream_t stream)
     if ((rc = dev_alloc(&p->d_cy, (size_t)p->n * (p->n - 1)))) return rc;
     if ((rc = dev_alloc(&p->d_cxf, (size_t)p->n * (p->n - 1)))) return rc;
     if ((rc = dev_alloc(&p->d_cyf, (size_t)p->n * (p->n - 1)))) return rc;
-    if ((rc = dev_alloc(&p->d_work, (size_t)nn * 9))) return rc;   // written before read
+    if ((rc = dev_alloc(&p->d_work, (size_t)nn * 11))) return rc;  // written before read
+    if ((rc = dev_alloc(&p->d_mg, (size_t)std::max<int64_t>(p->mg_floats, 1)))) return rc;
     if ((rc = dev_alloc(&p->d_subs, p->h_subs.size()))) return rc;
     if ((rc = dev_alloc(&p->d_substats, p->h_subs.size()))) return rc;
     SDD_CUDA(cudaMemcpyAsync(p->d_subs, p->h_subs.data(), p->h_subs.size() * sizeof(SubDev),
@@ -312,6 +319,41 @@ int validate_mc(const sdd_mc_params* mc)
     const double cap = mc->max_steps ? (double)mc->max_steps : std::ceil(2.0 / mc->dt);
     if (cap < 1.0 || cap > 4294967294.0)
         return fail(SDD_ERR_INVALID_ARG, "max_steps must be in [1, 2^32 - 2]");
+    if (mc->reserved != 0) return fail(SDD_ERR_INVALID_ARG, "reserved must be 0");
+    if (mc->path_begin) {
+        if (mc->path_begin > mc->paths_per_node)
+            return fail(SDD_ERR_INVALID_ARG, "path_begin must not exceed paths_per_node");
+        if (!mc->chunk || mc->path_begin % (uint64_t)mc->chunk)
+            return fail(SDD_ERR_INVALID_ARG,
+                        "a continued run needs an explicit chunk that divides path_begin");
+    }
+    return SDD_OK;
+}
+
+// A run with path_begin > 0 continues the plan's previous whole run: same
+// request and parameters but N, which must equal path_begin.
+int check_continuation(const sdd_plan* p, const sdd_mc_params* mc, int64_t nodes)
+{
+    if (!p->items_valid)
+        return fail(SDD_ERR_INVALID_ARG,
+                    "path_begin > 0 but the plan holds no previous whole run to continue");
+    const sdd_mc_params& q = p->items_mc;
+    auto cap = [](const sdd_mc_params& m) {
+        return m.max_steps ? m.max_steps : (uint64_t)std::ceil(2.0 / m.dt);
+    };
+    auto tie = [](const sdd_mc_params& m) {
+        return m.tie_delta >= 0.0 ? m.tie_delta : (m.precision == SDD_FP64 ? 1e-11 : 0.0);
+    };
+    if (q.paths_per_node != mc->path_begin)
+        return fail(SDD_ERR_INVALID_ARG, "path_begin (" + std::to_string(mc->path_begin) +
+                                             ") differs from the previous run's paths per node (" +
+                                             std::to_string(q.paths_per_node) + ")");
+    if (q.seed != mc->seed || q.dt != mc->dt || q.precision != mc->precision ||
+        q.chunk != mc->chunk || cap(q) != cap(*mc) || tie(q) != tie(*mc) ||
+        q.exit_test != mc->exit_test || q.stepper != mc->stepper || p->items_nodes != nodes)
+        return fail(SDD_ERR_INVALID_ARG,
+                    "path_begin > 0 but the previous run had other parameters than this one "
+                    "(seed, dt, precision, chunk, step cap, tie delta, exit test, stepper)");
     return SDD_OK;
 }
 
@@ -347,6 +389,7 @@ void mesh_record(const sdd_plan* p, const sdd_mc_params* mc, MeshDev& m)
     m.tab64 = p->d_tab64;
     m.cell32 = p->d_cell32;
     m.tn = p->dens.tn;
+    m.chunk_begin = mc->path_begin ? (uint32_t)(mc->path_begin / chunk) : 0u;
 }
 
 // Builds the mesh record and launches the path kernel + reduction.
@@ -383,6 +426,26 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     int rc = validate_mc(mc);
     if (rc) return rc;
     p->resume_active = false;                 // a whole run replaces any split one
+    const int64_t nodes = p->n_mc;
+    if (mc->path_begin) {
+        // continue the previous run: its items move to their places in this
+        // run's node-major layout (node v, chunk c at v * cpn + c)
+        if ((rc = check_continuation(p, mc, nodes))) return rc;
+        const uint32_t chunk = (uint32_t)mc->chunk;
+        const uint64_t cpn_prev = mc->path_begin / chunk;
+        const uint64_t cpn = (mc->paths_per_node + chunk - 1) / chunk;
+        AllocOn on(stream);
+        Slot* fresh = nullptr;
+        if ((rc = dev_alloc(&fresh, (size_t)(nodes * cpn)))) return rc;
+        if (nodes > 0)
+            SDD_CUDA(cudaMemcpy2DAsync(fresh, cpn * sizeof(Slot), p->d_slots, cpn_prev * sizeof(Slot),
+                                       cpn_prev * sizeof(Slot), (size_t)nodes,
+                                       cudaMemcpyDeviceToDevice, stream));
+        dev_free(p->d_slots, stream);
+        p->d_slots = fresh;
+        p->slots_cap = (uint64_t)nodes * cpn;
+    }
+    p->items_valid = false;
     McArgs a;
     bool few = false;
     if ((rc = mc_args(p, mc, mean_dev, stderr_dev, sums_dev, a, few, stream))) return rc;
@@ -390,6 +453,10 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     if ((rc = launch_mc(a, mc->precision, mesh_kernel_class(a.single.family, a.single.nb,
                                                             a.single.stepper), stream)))
         return rc;
+    p->items_valid = true;
+    p->items_mc = *mc;
+    p->items_nodes = nodes;
+    ++p->items_run;
     return mc_tail(p, mc, few, mean_dev, stderr_dev, stream);
 }
 
@@ -455,10 +522,17 @@ int read_mc_stats(sdd_plan* p, sdd_mc_stats* out, cudaStream_t stream)
     return stats_from_dev(s, p->last_paths * (uint64_t)p->n_mc, out);
 }
 
+// Bit of a solver in a launch's solver mask (1 SOR, 2 multigrid CG, 4 Jacobi CG).
+int solver_bit(int solver)
+{
+    return solver == SDD_SOLVER_SOR ? 1 : solver == SDD_SOLVER_CG_FP32_REFINE ? 2 : 4;
+}
+
 int validate_solve(const sdd_solve_params* sp)
 {
     if (!sp) return fail(SDD_ERR_INVALID_ARG, "solve params are NULL");
-    if (sp->solver != SDD_SOLVER_SOR && sp->solver != SDD_SOLVER_CG_FP32_REFINE)
+    if (sp->solver != SDD_SOLVER_SOR && sp->solver != SDD_SOLVER_CG_FP32_REFINE &&
+        sp->solver != SDD_SOLVER_CG_JACOBI_FP32_REFINE)
         return fail(SDD_ERR_INVALID_ARG, "unknown solver");
     if (!(sp->tol > 0.0) || !std::isfinite(sp->tol))
         return fail(SDD_ERR_INVALID_ARG, "tol must be positive");
@@ -492,6 +566,7 @@ int run_solve(sdd_plan* p, const double* iface_dev, const sdd_solve_params* sp,
     sm.cxf = p->d_cxf;
     sm.cyf = p->d_cyf;
     sm.work = p->d_work;
+    sm.mg = p->d_mg;
     if ((rc = launch_fill_mesh(p->n, p->d_edges, p->d_nodes, p->n_nodes, iface_dev, p->d_u,
                                p->d_subs, (int)p->h_subs.size(), stream)))
         return rc;
@@ -500,7 +575,7 @@ int run_solve(sdd_plan* p, const double* iface_dev, const sdd_solve_params* sp,
     a.single = sm;
     a.subs = p->d_subs;
     a.n_subs = (int)p->h_subs.size();
-    a.solver_mask = sp->solver == SDD_SOLVER_SOR ? 1 : 2;
+    a.solver_mask = solver_bit(sp->solver);
     a.threads = sp->block_threads;
     a.stats = p->d_substats;
     if ((rc = launch_solve(a, stream))) return rc;
@@ -519,11 +594,14 @@ int read_solve_stats(sdd_plan* p, sdd_solve_stats* out, cudaStream_t stream)
     out->converged = 0;
     out->max_iterations = 0;
     out->max_rel_residual = 0.0;
+    out->node_iterations = 0.0;
     for (const SubStat& s : st) {
         out->converged += s.converged;
         out->max_iterations = std::max(out->max_iterations, s.iterations);
         out->max_rel_residual = std::max(out->max_rel_residual, s.rel_residual);
     }
+    for (const SubDev& d : p->h_subs)
+        out->node_iterations += (double)st[d.slot].iterations * interior_nodes(d);
     return out->converged == out->subdomains
                ? SDD_OK
                : fail(SDD_ERR_NOT_CONVERGED, "a subdomain did not reach the tolerance");
@@ -655,6 +733,18 @@ struct McGroup {
     McArgs args;
 };
 
+// A plan whose run continues its previous single-plan run (path_begin > 0):
+// before the path kernels, the previous run's items (rows of cpn_prev slots
+// in the plan's buffer) are copied to their places in the batch's slots
+// (rows of cpn), where the path kernel skips them.
+struct SlotSeed {
+    const sdd_plan* plan;
+    uint64_t run;           // the plan's run whose items are copied (items_run)
+    const Slot* src;
+    uint64_t dst;           // first slot of the plan's mesh in the batch's slots
+    uint64_t cpn_prev, cpn, rows;
+};
+
 }  // namespace
 }  // namespace sdd
 
@@ -663,6 +753,7 @@ struct sdd_batch {
     std::vector<sdd_plan*> plans;
     std::vector<uint64_t> plan_paths;           // N per plan
     std::vector<sdd::McGroup> groups;
+    std::vector<sdd::SlotSeed> seeds;           // plans that continue a previous run
     std::vector<int> plan_slot;                 // plan -> index of its record in d_meshes
     sdd::MeshDev* d_meshes = nullptr;
     uint64_t* d_offs = nullptr;                 // item and node prefix sums of every group
@@ -710,6 +801,18 @@ void batch_free(sdd_batch* b)
     delete b;
 }
 
+// The plans that continue a previous run must still hold that run's items
+// where the batch was told they are.
+int check_seeds(const sdd_batch* b)
+{
+    for (const SlotSeed& q : b->seeds)
+        if (!q.plan->items_valid || q.plan->items_run != q.run || q.plan->d_slots != q.src)
+            return fail(SDD_ERR_INVALID_ARG,
+                        "a plan of the batch continues a run (path_begin > 0) whose work items "
+                        "it no longer holds (another Monte Carlo ran on it since)");
+    return SDD_OK;
+}
+
 // Enqueues one whole run of the batch on `stream` (no host synchronisation,
 // no device queries: safe inside a stream capture).
 int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
@@ -717,6 +820,11 @@ int batch_enqueue(sdd_batch* b, cudaStream_t stream, int phases = 3)
     const size_t np = b->plans.size();
     if (phases & 1) {
         SDD_CUDA(cudaMemsetAsync(b->d_stats, 0, np * sizeof(McStatsDev), stream));
+        for (const SlotSeed& q : b->seeds)
+            if (q.rows)
+                SDD_CUDA(cudaMemcpy2DAsync(b->d_slots + q.dst, q.cpn * sizeof(Slot), q.src,
+                                           q.cpn_prev * sizeof(Slot), q.cpn_prev * sizeof(Slot),
+                                           (size_t)q.rows, cudaMemcpyDeviceToDevice, stream));
         for (const McGroup& g : b->groups) {
             int rc = launch_mc_sized(g.args, g.precision, g.kc, g.blocks, stream);
             if (rc) return rc;
@@ -818,7 +926,10 @@ int sdd_mesh_plan(int n, int sx, int sy, const sdd_density* dens, const sdd_bmap
     for (int b = 0; b < sy; ++b)
         for (int a = 0; a < sx; ++a) {
             const int32_t slot = (int32_t)p->h_subs.size();
-            p->h_subs.push_back(SubDev{0, X[a], X[a + 1], Y[b], Y[b + 1], slot});
+            MgShape mg;
+            mg_shape(X[a + 1] - X[a] - 1, Y[b + 1] - Y[b] - 1, mg);
+            p->h_subs.push_back(SubDev{0, X[a], X[a + 1], Y[b], Y[b + 1], slot, p->mg_floats});
+            p->mg_floats += mg.total;
         }
     sort_largest_first(p->h_subs);
 
@@ -1027,9 +1138,12 @@ int sdd_interface_mc_advance(sdd_plan* p, const sdd_mc_params* mc, uint64_t max_
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = validate_mc(mc))) return rc;
+    if (mc->path_begin)
+        return fail(SDD_ERR_INVALID_ARG, "a split run starts at path 0 (path_begin must be 0)");
     cudaStream_t stream = as_stream(stream_);
     McArgs a;
     bool few = false;
+    p->items_valid = false;                      // the split run writes the item slots
     if ((rc = mc_args(p, mc, nullptr, nullptr, nullptr, a, few, stream))) return rc;
     if (!p->resume_active || !same_mc(p->resume_mc, *mc)) {     // a new split run
         p->resume_active = true;
@@ -1116,7 +1230,7 @@ int sdd_mc_checkpoint_save(sdd_plan* p, void* host, uint64_t bytes, void* stream
     CheckpointHeader h;
     memset(&h, 0, sizeof(h));
     h.magic = kCheckpointMagic;
-    h.version = 1;
+    h.version = 2;
     h.n = (uint64_t)p->n;
     h.n_mc = (uint64_t)p->n_mc;
     h.items_total = p->resume_total;
@@ -1141,7 +1255,7 @@ int sdd_mc_checkpoint_load(sdd_plan* p, const void* host, uint64_t bytes, void* 
         return fail(SDD_ERR_INVALID_ARG, "not a checkpoint (too short)");
     CheckpointHeader h;
     memcpy(&h, host, sizeof(h));
-    if (h.magic != kCheckpointMagic || h.version != 1 || h.slot_bytes != sizeof(Slot))
+    if (h.magic != kCheckpointMagic || h.version != 2 || h.slot_bytes != sizeof(Slot))
         return fail(SDD_ERR_INVALID_ARG, "not a checkpoint of this library");
     if (h.n != (uint64_t)p->n || h.n_mc != (uint64_t)p->n_mc || h.plan_hash != plan_hash(p))
         return fail(SDD_ERR_INVALID_ARG, "the checkpoint belongs to another plan");
@@ -1161,6 +1275,7 @@ int sdd_mc_checkpoint_load(sdd_plan* p, const void* host, uint64_t bytes, void* 
         SDD_CUDA(cudaMemcpyAsync(p->d_slots, static_cast<const unsigned char*>(host) + sizeof(h),
                                  h.items_done * sizeof(Slot), cudaMemcpyHostToDevice, stream));
     SDD_CUDA(cudaStreamSynchronize(stream));
+    p->items_valid = false;                      // the slots hold the checkpoint's items
     p->resume_active = true;
     p->resume_mc = h.mc;
     p->resume_next = h.items_done;
@@ -1276,6 +1391,7 @@ void sdd_plan_destroy(sdd_plan* p)
     dev_free(p->d_cxf, fs);
     dev_free(p->d_cyf, fs);
     dev_free(p->d_work, fs);
+    dev_free(p->d_mg, fs);
     dev_free(p->d_subs, fs);
     dev_free(p->d_substats, fs);
     dev_free(p->d_mc_nodes, fs);
@@ -1324,6 +1440,7 @@ int sdd_plan_set_placement(sdd_plan* p, int mode, int k)
     p->place_mode = mode;
     p->h_mask = mask;
     p->n_mc = (int64_t)ids.size();
+    p->items_valid = false;                             // other Monte Carlo nodes
     if (p->n_mc == p->n_nodes) return SDD_OK;           // every node: the plain path
     if ((rc = ensure_mc_buffers(p, 0, ss))) return rc;
     std::vector<InterpEntry> ent = interp_entries(p, mask);
@@ -1569,6 +1686,16 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
                     m.chunks_per_node = (uint32_t)((mc[i].paths_per_node + m.chunk - 1) / m.chunk);
                 }
             }
+            if (mc[i].path_begin) {
+                if ((rc = check_continuation(plans[i], &mc[i], m.n_nodes))) {
+                    batch_free(b);
+                    return rc;
+                }
+                b->seeds.push_back(SlotSeed{plans[i], plans[i]->items_run, plans[i]->d_slots,
+                                            slot_total + it,
+                                            mc[i].path_begin / m.chunk, m.chunks_per_node,
+                                            (uint64_t)m.n_nodes});
+            }
             m.item_begin = it;
             offs.push_back(it);
             it += (uint64_t)m.n_nodes * m.chunks_per_node;
@@ -1600,7 +1727,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         memset(&r, 0, sizeof(r));
         r.n = p->n;
         r.solver = sp[i].solver;
-        b->solver_mask |= sp[i].solver == SDD_SOLVER_SOR ? 1 : 2;
+        b->solver_mask |= solver_bit(sp[i].solver);
         b->solve_threads = std::max(b->solve_threads, (int)sp[i].block_threads);
         r.max_iter = sp[i].max_iter > 0 ? sp[i].max_iter : (sp[i].solver == SDD_SOLVER_SOR ? 200000 : 20000);
         r.tol = sp[i].tol;
@@ -1611,6 +1738,7 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
         r.cxf = p->d_cxf;
         r.cyf = p->d_cyf;
         r.work = p->d_work;
+        r.mg = p->d_mg;
         FillDev& f = fill[i];
         memset(&f, 0, sizeof(f));
         f.n = p->n;
@@ -1719,6 +1847,7 @@ int sdd_batch_run(sdd_batch* b, int use_graph, void* stream_)
     if (dev != b->device) return fail(SDD_ERR_INVALID_ARG, "batch belongs to another device");
     cudaStream_t stream = as_stream(stream_);
     int rc;
+    if ((rc = check_seeds(b))) return rc;
     if (use_graph) {
         if (stream == nullptr)
             return fail(SDD_ERR_INVALID_ARG, "a graph launch needs a non-default stream");
@@ -1768,7 +1897,9 @@ int sdd_batch_run_phases(sdd_batch* b, int phases, void* stream_)
     SDD_CUDA(cudaGetDevice(&dev));
     if (dev != b->device) return fail(SDD_ERR_INVALID_ARG, "batch belongs to another device");
     cudaStream_t stream = as_stream(stream_);
-    int rc = batch_enqueue(b, stream, phases);
+    int rc = (phases & 1) ? check_seeds(b) : SDD_OK;
+    if (rc) return rc;
+    rc = batch_enqueue(b, stream, phases);
     if (rc) return rc;
     if (phases & 1) {
         for (size_t i = 0; i < b->plans.size(); ++i) {
@@ -1811,11 +1942,14 @@ int sdd_batch_plan_stats(sdd_batch* b, int index, sdd_mc_stats* mc, sdd_solve_st
         solve->converged = 0;
         solve->max_iterations = 0;
         solve->max_rel_residual = 0.0;
+        solve->node_iterations = 0.0;
         for (const SubStat& x : st) {
             solve->converged += x.converged;
             solve->max_iterations = std::max(solve->max_iterations, x.iterations);
             solve->max_rel_residual = std::max(solve->max_rel_residual, x.rel_residual);
         }
+        for (const SubDev& d : p->h_subs)
+            solve->node_iterations += (double)st[d.slot].iterations * interior_nodes(d);
         if (solve->converged != solve->subdomains)
             return fail(SDD_ERR_NOT_CONVERGED, "a subdomain did not reach the tolerance");
     }
@@ -1879,24 +2013,99 @@ constexpr uint64_t kStaticMaxItems = (kStaticScratchBytes - kStaticHeadBytes) / 
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_mu;
-void* g_static_ptr[64] = {};
+// Driver calls reached through the runtime's entry-point lookup, so that the
+// library does not link libcuda (it still loads on machines without a GPU).
+using MemRangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+using CtxCurrentFn = CUresult (*)(CUcontext*);
+using CtxIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the array for the current device: looked up once per
-// device (the first call on a device), with that device current.
-int static_scratch(void** out)
+template <typename F>
+int driver_fn(const char* name, F* out)
+{
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) {
+        cudaGetLastError();
+        return fail(SDD_ERR_CUDA, std::string("driver entry point ") + name + " not available");
+    }
+    *out = reinterpret_cast<F>(f);
+    return SDD_OK;
+}
+
+struct StaticState {
+    void* ptr = nullptr;              // device address of the array in this context
+    unsigned long long ctx = 0;       // id of the context it was looked up in
+    uint64_t paths = 0;               // paths of the last call, all nodes (statistics)
+};
+std::mutex g_static_mu;
+StaticState g_static[64];
+
+// Device address of the array for the current device: looked up with that
+// device current on the first call, and again whenever the device's current
+// context is another one than at the last lookup (after a cudaDeviceReset
+// the array lives at a new address).
+int static_scratch(void** out, int* dev_out)
 {
     int dev = -1;
     SDD_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(SDD_ERR_NO_DEVICE, "device index out of range");
+    SDD_CUDA(cudaSetDevice(dev));                    // initialises the device's primary context
+    static CtxCurrentFn ctx_current = nullptr;
+    static CtxIdFn ctx_id = nullptr;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    int rc;
+    if (!ctx_current && (rc = driver_fn("cuCtxGetCurrent", &ctx_current))) return rc;
+    if (!ctx_id && (rc = driver_fn("cuCtxGetId", &ctx_id))) return rc;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (ctx_current(&ctx) != CUDA_SUCCESS || !ctx || ctx_id(ctx, &id) != CUDA_SUCCESS)
+        return fail(SDD_ERR_CUDA, "no current CUDA context for the static scratch");
+    StaticState& st = g_static[dev];
+    if (!st.ptr || st.ctx != id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
-        g_static_ptr[dev] = p;
+        st.ptr = p;
+        st.ctx = id;
     }
-    *out = g_static_ptr[dev];
+    *out = st.ptr;
+    *dev_out = dev;
+    return SDD_OK;
+}
+
+// A caller's buffer must be device (or managed) memory of the current device,
+// aligned for its element type, and hold `bytes` bytes from `p` on within its
+// allocation (cuMemGetAddressRange), so that no kernel of the call can read
+// or write outside it.
+int check_span(const void* p, size_t bytes, size_t align, int dev, const char* name)
+{
+    if (reinterpret_cast<uintptr_t>(p) % align)
+        return fail(SDD_ERR_INVALID_ARG, std::string(name) + " must be aligned to " +
+                                             std::to_string(align) + " bytes");
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) cudaGetLastError();
+    if (e != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged))
+        return fail(SDD_ERR_INVALID_ARG, std::string(name) + " must be device memory");
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(SDD_ERR_INVALID_ARG, std::string(name) + " is memory of another device");
+    static MemRangeFn range = nullptr;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!range && (rc = driver_fn("cuMemGetAddressRange", &range))) return rc;
+    }
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (range(&base, &size, (CUdeviceptr)reinterpret_cast<uintptr_t>(p)) != CUDA_SUCCESS)
+        return fail(SDD_ERR_INVALID_ARG, std::string(name) + ": no device allocation holds it");
+    const uint64_t have = (uint64_t)base + size - (uint64_t)reinterpret_cast<uintptr_t>(p);
+    if (have < bytes)
+        return fail(SDD_ERR_INVALID_ARG, std::string(name) + " needs " + std::to_string(bytes) +
+                                             " bytes, its allocation holds " +
+                                             std::to_string(have) + " from the pointer on");
     return SDD_OK;
 }
 
@@ -1919,9 +2128,8 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
                     "the allocation-free entry point takes the analytic families only "
                     "(a TABLE density is copied to the device by a plan)");
     if ((rc = validate_mc(mc))) return rc;
-    if (!is_device_ptr(nodes) || !is_device_ptr(edges) || !is_device_ptr(mean) ||
-        (stderr_ && !is_device_ptr(stderr_)))
-        return fail(SDD_ERR_INVALID_ARG, "nodes, edges, mean and stderr_ must be device memory");
+    if (mc->path_begin)
+        return fail(SDD_ERR_INVALID_ARG, "the allocation-free entry point takes path_begin = 0");
     // work-item size: the caller's, else the automatic one, raised (up to 8192
     // paths) until the work items fit the static array
     uint32_t chunk = mc->chunk ? (uint32_t)mc->chunk : auto_chunk(mc->paths_per_node, n_nodes);
@@ -1938,7 +2146,14 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
                         std::to_string(items) + " work items, at most " +
                         std::to_string(kStaticMaxItems) + " fit in 8 MiB");
     void* base = nullptr;
-    if ((rc = static_scratch(&base))) return rc;
+    int dev = -1;
+    if ((rc = static_scratch(&base, &dev))) return rc;
+    const size_t node_bytes = (size_t)n_nodes * 2 * sizeof(double);
+    if ((rc = check_span(nodes, (size_t)n_nodes * 2 * sizeof(int32_t), 8, dev, "nodes")) ||
+        (rc = check_span(edges, (size_t)8 * n * sizeof(double), 8, dev, "edges")) ||
+        (rc = check_span(mean, node_bytes, 8, dev, "mean")) ||
+        (stderr_ && (rc = check_span(stderr_, node_bytes, 8, dev, "stderr_"))))
+        return rc;
     unsigned char* b = static_cast<unsigned char*>(base);
     cudaStream_t stream = as_stream(stream_);
 
@@ -1980,5 +2195,32 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
     a.queue = reinterpret_cast<unsigned long long*>(b);          // zeroed by the launcher
     a.slots = reinterpret_cast<Slot*>(b + kStaticHeadBytes);     // written before read
     SDD_CUDA(cudaMemsetAsync(m.stats, 0, sizeof(McStatsDev), stream));
-    return launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper), stream);
+    rc = launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper), stream);
+    if (rc == SDD_OK) {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        g_static[dev].paths = mc->paths_per_node * (uint64_t)n_nodes;   // paths of all nodes
+    }
+    return rc;
+}
+
+extern "C" int sdd_interface_mc_static_stats(sdd_mc_stats* stats, void* stream_)
+{
+    clear_error();
+    if (!stats) return fail(SDD_ERR_INVALID_ARG, "stats is NULL");
+    void* base = nullptr;
+    int dev = -1;
+    int rc = static_scratch(&base, &dev);
+    if (rc) return rc;
+    uint64_t paths;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        paths = g_static[dev].paths;
+    }
+    if (!paths) return fail(SDD_ERR_INVALID_ARG, "no allocation-free Monte Carlo call on this device yet");
+    McStatsDev h;
+    cudaStream_t stream = as_stream(stream_);
+    SDD_CUDA(cudaMemcpyAsync(&h, static_cast<unsigned char*>(base) + 256, sizeof(h),
+                             cudaMemcpyDeviceToHost, stream));
+    SDD_CUDA(cudaStreamSynchronize(stream));
+    return stats_from_dev(h, paths, stats);
 }

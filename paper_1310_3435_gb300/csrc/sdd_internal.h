@@ -70,7 +70,8 @@ struct MeshDev {
     const float4* cell32;   // FP32 stepping: per cell (c1, c2, c3, 0) with L = c0 + (c1 fa +
                             // c2 fb + c3 fa fb) / (tn-1) in the cell's local coordinates
     int32_t tn;
-    int32_t pad1;
+    uint32_t chunk_begin;   // items of a node with chunk index < chunk_begin hold the
+                            // sums of the run this one continues: not run again
 };
 
 // Partial sums of one work item (one chunk of paths of one node).
@@ -170,14 +171,62 @@ struct SolveMeshDev {
     const double* cy;       // [n-1][n]  c at (i, j+1/2)
     const float* cxf;       // FP32 copies
     const float* cyf;
-    float* work;            // FP32 workspace, 9 floats per grid node (r p q x: 2 each, 1/diag)
+    float* work;            // FP32 workspace, 11 floats per grid node (r p q x z: 2 each, 1/diag)
+    float* mg;              // multigrid levels of the subdomains (SubDev::mg_off)
 };
 
 struct SubDev {
     int32_t mesh;           // index into the SolveMeshDev array
     int32_t i0, i1, j0, j1; // interior: i0 < i < i1, j0 < j < j1
     int32_t slot;           // index of its SubStat record
+    int64_t mg_off;         // first float of its multigrid levels in the mesh's mg buffer
 };
+
+// ------------------------------------------------ multigrid hierarchy --
+// Coarse levels of a subdomain's geometric multigrid, the preconditioner of
+// the FP32 CG.  Level 0 is the subdomain's interior (nx x ny nodes); level
+// l + 1 halves (floor) each side of level l that has at least 2 nodes, until
+// a level holds at most MG_COARSEST nodes or cannot shrink.  A coarse level
+// is stored with a ring of padding around its interior (pitch nx + 2): the
+// 9 planes of its Galerkin stencil (float), then the planes x, b, t
+// (float2), each plane `plane` floats (even, so float2 planes stay aligned).
+constexpr int MG_MAX_LEVELS = 16;
+constexpr int MG_COARSEST = 32;
+
+struct MgShape {
+    int levels;                        // coarse levels (0: none)
+    int nx[MG_MAX_LEVELS], ny[MG_MAX_LEVELS];   // [0]: the interior
+    int cx[MG_MAX_LEVELS], cy[MG_MAX_LEVELS];   // level l was coarsened in x / in y
+    int plane[MG_MAX_LEVELS];          // floats per plane of level l (l >= 1)
+    int64_t off[MG_MAX_LEVELS];        // first float of level l (l >= 1)
+    int64_t total;                     // floats of all coarse levels
+};
+
+__host__ __device__ inline void mg_shape(int nx, int ny, MgShape& s)
+{
+    s.levels = 0;
+    s.total = 0;
+    s.nx[0] = nx > 0 ? nx : 0;
+    s.ny[0] = ny > 0 ? ny : 0;
+    s.cx[0] = s.cy[0] = 0;
+    s.plane[0] = 0;
+    s.off[0] = 0;
+    int l = 0;
+    while (l + 1 < MG_MAX_LEVELS && s.nx[l] * s.ny[l] > MG_COARSEST) {
+        const int cx = s.nx[l] >= 2, cy = s.ny[l] >= 2;
+        if (!cx && !cy) break;
+        ++l;
+        s.nx[l] = cx ? s.nx[l - 1] / 2 : s.nx[l - 1];
+        s.ny[l] = cy ? s.ny[l - 1] / 2 : s.ny[l - 1];
+        s.cx[l] = cx;
+        s.cy[l] = cy;
+        const int a = (s.nx[l] + 2) * (s.ny[l] + 2);
+        s.plane[l] = a + (a & 1);
+        s.off[l] = s.total;
+        s.total += 15 * (int64_t)s.plane[l];
+    }
+    s.levels = l;
+}
 
 struct SubStat {
     int32_t iterations;
@@ -200,7 +249,7 @@ struct SolveArgs {
     SolveMeshDev single;
     const SubDev* subs;
     int n_subs;
-    int solver_mask;            // bit 0: some subdomain uses SOR, bit 1: CG
+    int solver_mask;            // bit 0: some subdomain uses SOR, bit 1: multigrid CG, bit 2: Jacobi CG
     int threads;                // CTA size: 256, 512 or 1024 (other: 1024)
     SubStat* stats;
 };
@@ -258,6 +307,12 @@ struct sdd_plan {
     sdd_mc_params resume_mc{};
     uint64_t resume_next = 0, resume_total = 0;
     cudaEvent_t mc_done = nullptr;         // recorded after each single-plan Monte Carlo call
+    // the run whose work items d_slots holds (the last whole single-plan run),
+    // which a later run may continue (sdd_mc_params.path_begin)
+    bool items_valid = false;
+    sdd_mc_params items_mc{};
+    int64_t items_nodes = 0;               // nodes the run ran on (few-point aware)
+    uint64_t items_run = 0;                // whole single-plan runs so far (identifies the items)
 
     // subdomain solves
     double* d_u = nullptr;
@@ -266,6 +321,8 @@ struct sdd_plan {
     float* d_cxf = nullptr;
     float* d_cyf = nullptr;
     float* d_work = nullptr;
+    float* d_mg = nullptr;                 // multigrid levels of all subdomains
+    int64_t mg_floats = 0;
     sdd::SubDev* d_subs = nullptr;
     sdd::SubStat* d_substats = nullptr;
     bool coefs_ready = false;

@@ -9,8 +9,10 @@
 // u is FP64 [n][n][2] (the two components share the operator and are solved
 // together, interleaved as double2).  Two solvers:
 //   * red-black SOR in FP64;
-//   * FP32 Jacobi-preconditioned CG for the correction A d = r, wrapped in FP64
-//     iterative refinement (FP64 residual r = b - A u, u += d).
+//   * FP32 CG for the correction A d = r, wrapped in FP64 iterative
+//     refinement (FP64 residual r = b - A u, u += d), preconditioned by a
+//     geometric multigrid V-cycle (Galerkin coarse operators) or by the
+//     diagonal (Jacobi).
 // Each CTA iterates to its relative residual ||b - A u||_2 / ||b||_2 <= tol,
 // stagnation or the iteration cap; the loops are bounded, never spin.
 #include <cuda_runtime.h>
@@ -21,6 +23,7 @@
 #include <utility>
 
 #include "sdd_internal.h"
+#include "mg.cuh"
 
 namespace sdd {
 namespace {
@@ -342,21 +345,145 @@ __device__ void sor_box(const SolveMeshDev& M, const Box& B, SubStat& st, double
 }
 
 // ------------------------------------------- FP32 PCG + FP64 refinement ----
-// Workspace per grid node (floats): r(2) p(2) q(2) x(2) dinv(1) pad(1).
-struct Work {
-    float2* r; float2* p; float2* q; float2* x; float* dinv;
-};
-
-__device__ __forceinline__ Work work_of(const SolveMeshDev& M)
+// FP32 CG preconditioned by the V-cycle, for the correction A d = r of each
+// round of FP64 iterative refinement (u += d, r = b - A u in FP64).  Both
+// components are solved together with their own step lengths.
+__device__ void cg_mg_box(const SolveMeshDev& M, const Box& B, float* mg_base, SubStat& st,
+                          double* scratch)
 {
-    const int64_t nn = (int64_t)M.n * M.n;
-    Work w;
-    w.r = reinterpret_cast<float2*>(M.work);
-    w.p = w.r + nn;
-    w.q = w.p + nn;
-    w.x = w.q + nn;
-    w.dinv = reinterpret_cast<float*>(w.x + nn);
-    return w;
+    __shared__ MgShape S;
+    const int n = B.n;
+    double2* __restrict__ u = reinterpret_cast<double2*>(M.u);
+    const Work W = work_of(M);
+    const float* __restrict__ cxf = M.cxf;
+    const float* __restrict__ cyf = M.cyf;
+    const int m = B.nx * B.ny;
+    float* fs = reinterpret_cast<float*>(scratch);
+    const Fine f{n, B.i0, B.j0, B.nx, B.ny, cxf, cyf};
+    if (threadIdx.x == 0) mg_shape(B.nx, B.ny, S);
+
+    // p = z = 0 on the ring: the SpMV and the smoothers read them there.
+    for (int t = threadIdx.x; t < 2 * (B.nx + B.ny) + 4; t += blockDim.x) {
+        int i, j;
+        if (t < B.nx + 2) { i = B.i0 + t; j = B.j0; }
+        else if (t < 2 * (B.nx + 2)) { i = B.i0 + (t - B.nx - 2); j = B.j1; }
+        else if (t < 2 * (B.nx + 2) + B.ny) { i = B.i0; j = B.j0 + 1 + (t - 2 * (B.nx + 2)); }
+        else { i = B.i1; j = B.j0 + 1 + (t - 2 * (B.nx + 2) - B.ny); }
+        W.p[(int64_t)j * n + i] = make_float2(0.f, 0.f);
+        W.z[(int64_t)j * n + i] = make_float2(0.f, 0.f);
+    }
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+        const int64_t id = (int64_t)j * n + i;
+        const float d = cxf[(int64_t)j * (n - 1) + i] + cxf[(int64_t)j * (n - 1) + i - 1] +
+                        cyf[id] + cyf[id - n];
+        W.dinv[id] = 1.0f / d;
+    }
+    __syncthreads();
+    mg_setup(f, mg_base, S);
+    const double b2 = rhs_norm2(M, B, scratch);
+    const double goal = M.tol * M.tol * fmax(b2, 1e-300);
+    const int max_inner = M.max_iter;
+    const float inner_tol2 = 1e-10f;          // FP32 inner solve: ||r||_M / ||r0||_M <= 1e-5
+    int total = 0;
+    double r2 = 0.0, best = INFINITY;
+    int rounds = 0, stall = 0;
+    for (rounds = 0; rounds < 40; ++rounds) {
+        // FP64 residual, cast to FP32; x = 0
+        double acc[1] = {0.0};
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+            const int64_t id = (int64_t)j * n + i;
+            const double2 r = residual64(M, u, n, i, j);
+            acc[0] += r.x * r.x + r.y * r.y;
+            W.r[id] = make_float2((float)r.x, (float)r.y);
+            W.x[id] = make_float2(0.f, 0.f);
+        }
+        block_sum<double, 1>(acc, scratch);
+        r2 = acc[0];
+        if (r2 <= goal) break;
+        if (r2 < 0.5 * best) { best = r2; stall = 0; }
+        else if (++stall >= 3) break;          // refinement no longer gains
+        mg_vcycle(f, W, mg_base, S);           // z = M^-1 r
+        float rz[2] = {0.f, 0.f};
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int64_t id = (int64_t)(B.j0 + 1 + t / B.nx) * n + (B.i0 + 1 + t % B.nx);
+            const float2 r = W.r[id], z = W.z[id];
+            W.p[id] = z;
+            rz[0] += r.x * z.x;
+            rz[1] += r.y * z.y;
+        }
+        block_sum<float, 2>(rz, fs + 64);
+        const float rz0 = fmaxf(rz[0], rz[1]);
+        float rzc[2] = {rz[0], rz[1]};
+        int it = 0;
+        for (; it < max_inner; ++it) {
+            __syncthreads();                   // p complete before the SpMV
+            float pq[2] = {0.f, 0.f};
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+                const int64_t id = (int64_t)j * n + i;
+                const float cE = cxf[(int64_t)j * (n - 1) + i], cW = cxf[(int64_t)j * (n - 1) + i - 1];
+                const float cN = cyf[id], cS = cyf[id - n];
+                const float2 c = W.p[id], e = W.p[id + 1], w = W.p[id - 1];
+                const float2 nn = W.p[id + n], s = W.p[id - n];
+                const float d = cE + cW + cN + cS;
+                float2 q;
+                q.x = d * c.x - (cE * e.x + cW * w.x + cN * nn.x + cS * s.x);
+                q.y = d * c.y - (cE * e.y + cW * w.y + cN * nn.y + cS * s.y);
+                W.q[id] = q;
+                pq[0] += c.x * q.x;
+                pq[1] += c.y * q.y;
+            }
+            block_sum<float, 2>(pq, fs);
+            const float al0 = pq[0] > 0.f ? rzc[0] / pq[0] : 0.f;
+            const float al1 = pq[1] > 0.f ? rzc[1] / pq[1] : 0.f;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int64_t id = (int64_t)(B.j0 + 1 + t / B.nx) * n + (B.i0 + 1 + t % B.nx);
+                const float2 p = W.p[id], q = W.q[id];
+                float2 x = W.x[id], r = W.r[id];
+                x.x += al0 * p.x; x.y += al1 * p.y;
+                r.x -= al0 * q.x; r.y -= al1 * q.y;
+                W.x[id] = x;
+                W.r[id] = r;
+            }
+            __syncthreads();                   // r complete before the V-cycle
+            mg_vcycle(f, W, mg_base, S);
+            float nz[2] = {0.f, 0.f};
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int64_t id = (int64_t)(B.j0 + 1 + t / B.nx) * n + (B.i0 + 1 + t % B.nx);
+                const float2 r = W.r[id], z = W.z[id];
+                nz[0] += r.x * z.x;
+                nz[1] += r.y * z.y;
+            }
+            block_sum<float, 2>(nz, fs + 64);
+            const float be0 = rzc[0] > 0.f ? nz[0] / rzc[0] : 0.f;
+            const float be1 = rzc[1] > 0.f ? nz[1] / rzc[1] : 0.f;
+            rzc[0] = nz[0];
+            rzc[1] = nz[1];
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int64_t id = (int64_t)(B.j0 + 1 + t / B.nx) * n + (B.i0 + 1 + t % B.nx);
+                const float2 z = W.z[id], p = W.p[id];
+                W.p[id] = make_float2(z.x + be0 * p.x, z.y + be1 * p.y);
+            }
+            if (fmaxf(rzc[0], rzc[1]) <= inner_tol2 * rz0) { ++it; break; }
+        }
+        total += it;
+        __syncthreads();
+        for (int t = threadIdx.x; t < m; t += blockDim.x) {
+            const int i = B.i0 + 1 + t % B.nx, j = B.j0 + 1 + t / B.nx;
+            const int64_t id = (int64_t)j * n + i;
+            const float2 x = W.x[id];
+            double2 v = u[id];
+            v.x += (double)x.x;
+            v.y += (double)x.y;
+            u[id] = v;
+        }
+        __syncthreads();
+    }
+    st.iterations = total;
+    st.rel_residual = sqrt(r2 / fmax(b2, 1e-300));
+    st.converged = r2 <= goal ? 1 : 0;
 }
 
 __device__ void cg_box(const SolveMeshDev& M, const Box& B, SubStat& st, double* scratch)
@@ -501,10 +628,12 @@ k_solve(SolveArgs a)
     st.converged = 1;
     st.rel_residual = 0.0;
     if (B.nx > 0 && B.ny > 0) {
-        if constexpr (MASK == 2) cg_box(M, B, st, scratch);
+        if constexpr (MASK == 2) cg_mg_box(M, B, M.mg + sd.mg_off, st, scratch);
         else if constexpr (MASK == 1) sor_box(M, B, st, scratch);
+        else if constexpr (MASK == 4) cg_box(M, B, st, scratch);
         else {
-            if (M.solver == SDD_SOLVER_CG_FP32_REFINE) cg_box(M, B, st, scratch);
+            if (M.solver == SDD_SOLVER_CG_FP32_REFINE) cg_mg_box(M, B, M.mg + sd.mg_off, st, scratch);
+            else if (M.solver == SDD_SOLVER_CG_JACOBI_FP32_REFINE) cg_box(M, B, st, scratch);
             else sor_box(M, B, st, scratch);
         }
     }
@@ -584,7 +713,7 @@ __global__ void __launch_bounds__(256) k_quality(QualityArgs a, const double2* _
     }
 }
 
-// Perona-Malik smoothing (§3.5, eq. PeronaMalikDiffusion), one FTCS step
+// Perona-Malik smoothing (§3.4, eq. PeronaMalikDiffusion), one FTCS step
 // u -> v per launch, both components: each of a node's four edges conducts
 // with g = exp(-(d/h)^2 / k^2) of its own difference d = u_nb - u, so
 //   v = u + r (g_E d_E + g_W d_W + g_N d_N + g_S d_S),  r = dt / h^2;
@@ -712,10 +841,15 @@ int launch_solve(const SolveArgs& args, cudaStream_t stream)
     SDD_CUDA(cudaGetLastError());
     count_launch();
     const int t = args.threads == 256 || args.threads == 512 ? args.threads : SOLVE_THREADS_DEFAULT;
+    // one solver in the launch: a kernel with that solver only; a mix: all three
     void (*k)(SolveArgs) = nullptr;
-    if (t == 256) k = args.solver_mask == 1 ? k_solve<1, 256> : args.solver_mask == 2 ? k_solve<2, 256> : k_solve<3, 256>;
-    else if (t == 512) k = args.solver_mask == 1 ? k_solve<1, 512> : args.solver_mask == 2 ? k_solve<2, 512> : k_solve<3, 512>;
-    else k = args.solver_mask == 1 ? k_solve<1, 1024> : args.solver_mask == 2 ? k_solve<2, 1024> : k_solve<3, 1024>;
+    const int sm = args.solver_mask;
+    if (t == 256)
+        k = sm == 1 ? k_solve<1, 256> : sm == 2 ? k_solve<2, 256> : sm == 4 ? k_solve<4, 256> : k_solve<7, 256>;
+    else if (t == 512)
+        k = sm == 1 ? k_solve<1, 512> : sm == 2 ? k_solve<2, 512> : sm == 4 ? k_solve<4, 512> : k_solve<7, 512>;
+    else
+        k = sm == 1 ? k_solve<1, 1024> : sm == 2 ? k_solve<2, 1024> : sm == 4 ? k_solve<4, 1024> : k_solve<7, 1024>;
     k<<<args.n_subs, t, 0, stream>>>(args);
     SDD_CUDA(cudaGetLastError());
     count_launch();

@@ -33,7 +33,7 @@ SDD_MAX_BUMPS, SDD_MAX_PARAMS = 6, 32
 SDD_COEF_W, SDD_COEF_INV_W = 0, 1
 SDD_BMAP_IDENTITY, SDD_BMAP_PAPER_1D, SDD_BMAP_TABLE = 0, 1, 2
 SDD_FP64, SDD_FP32_STEP = 0, 1
-SDD_SOLVER_SOR, SDD_SOLVER_CG_FP32_REFINE = 0, 1
+SDD_SOLVER_SOR, SDD_SOLVER_CG_FP32_REFINE, SDD_SOLVER_CG_JACOBI_FP32_REFINE = 0, 1, 2
 SDD_EXIT_END_OF_STEP, SDD_EXIT_BRIDGE = 0, 1
 SDD_STEP_EULER, SDD_STEP_EXPONENTIAL = 0, 1
 SDD_PLACE_ALL, SDD_PLACE_EQUISPACED, SDD_PLACE_EXTREMA = 0, 1, 2
@@ -62,7 +62,8 @@ class sdd_mc_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("max_steps", ctypes.c_uint64),
                 ("tie_delta", ctypes.c_double), ("exit_test", ctypes.c_int32),
-                ("stepper", ctypes.c_int32)]
+                ("stepper", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("path_begin", ctypes.c_uint64)]
 
 
 class sdd_mc_stats(ctypes.Structure):
@@ -102,7 +103,7 @@ class sdd_quality(ctypes.Structure):
 class sdd_solve_stats(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int32), ("subdomains", ctypes.c_int32),
                 ("max_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("max_rel_residual", ctypes.c_double)]
+                ("max_rel_residual", ctypes.c_double), ("node_iterations", ctypes.c_double)]
 
 
 _lib = None
@@ -162,6 +163,7 @@ def load(build_if_missing: bool = True):
     L.sdd_batch_destroy.restype = None
     L.sdd_interface_mc_static.argtypes = [ctypes.c_int, vp, ctypes.c_int64, vp, P(sdd_density),
                                           P(sdd_mc_params), vp, vp, vp]
+    L.sdd_interface_mc_static_stats.argtypes = [P(sdd_mc_stats), vp]
     L.sdd_plan_set_placement.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.sdd_plan_placement.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.sdd_mesh_quality.argtypes = [vp, vp, vp, P(sdd_quality), vp]
@@ -178,7 +180,8 @@ def load(build_if_missing: bool = True):
                  "sdd_interface_mc", "sdd_interface_mc_sums", "sdd_plan_last_mc_stats",
                  "sdd_subdomain_solve", "sdd_mesh_generate", "sdd_kernel_launches",
                  "sdd_plan_results", "sdd_batch_create", "sdd_batch_run", "sdd_batch_run_phases",
-                 "sdd_batch_plan_stats", "sdd_interface_mc_static", "sdd_plan_set_placement",
+                 "sdd_batch_plan_stats", "sdd_interface_mc_static",
+                 "sdd_interface_mc_static_stats", "sdd_plan_set_placement",
                  "sdd_plan_placement", "sdd_mesh_quality", "sdd_mesh_smooth",
                  "sdd_mesh_smooth_subdomains", "sdd_interface_mc_advance", "sdd_interface_mc_finish", "sdd_mc_checkpoint_bytes",
                  "sdd_mc_checkpoint_save", "sdd_mc_checkpoint_load"):
@@ -284,7 +287,7 @@ def sdd_plan_edges(plan, n: int) -> np.ndarray:
 def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, chunk: int = 0,
               max_steps: int = 0, tie_delta: float = -1.0,
               exit_test: int = SDD_EXIT_END_OF_STEP,
-              stepper: int = SDD_STEP_EULER) -> sdd_mc_params:
+              stepper: int = SDD_STEP_EULER, path_begin: int = 0) -> sdd_mc_params:
     m = sdd_mc_params()
     m.paths_per_node = int(paths)
     m.dt = float(dt)
@@ -295,6 +298,7 @@ def mc_params(paths: int, dt: float, seed: int = 0, precision: int = SDD_FP64, c
     m.tie_delta = float(tie_delta)
     m.exit_test = int(exit_test)
     m.stepper = int(stepper)
+    m.path_begin = int(path_begin)
     return m
 
 
@@ -405,6 +409,15 @@ def sdd_interface_mc_static(n: int, nodes, edges, density: sdd_density, mc: sdd_
                                           ctypes.byref(density), ctypes.byref(mc), _ptr(mean),
                                           _ptr(stderr), _stream(stream)),
            "sdd_interface_mc_static")
+
+
+def sdd_interface_mc_static_stats(stream=None) -> sdd_mc_stats:
+    """Statistics of the last allocation-free call on the current device
+    (synchronises `stream`)."""
+    st = sdd_mc_stats()
+    _check(load().sdd_interface_mc_static_stats(ctypes.byref(st), _stream(stream)),
+           "sdd_interface_mc_static_stats")
+    return st
 
 
 def sdd_plan_set_placement(plan, mode: int, k: int = 7) -> None:

@@ -12,7 +12,11 @@ device. Completed batches are polled through CUDA events. Their plans are
 released stream-ordered, and the memory budget is handed back.
 
 Every request keeps its own Philox key and work-item size, so its result is
-bitwise the same alone and in any mix (see tests/test_gpu_serving.py).
+bitwise the same alone and in any mix (see tests/test_gpu_serving.py).  The
+pilot's paths are not thrown away: the estimator is a sum over paths, so the
+final run continues the pilot (sdd_mc_params.path_begin) and runs only the
+paths the pilot did not, with a result bitwise equal to one run of N paths
+of the same work-item size.
 PyTorch is used for streams, events and pinned host buffers only.
 
 Failures stay with the requests they hit: a request whose plan or pilot
@@ -74,13 +78,16 @@ def auto_chunk_host(paths: int, n_nodes: int, sms: int) -> int:
     return min(c, ((paths + 31) // 32) * 32)
 
 
-def device_bytes(n: int, n_nodes: int, paths: int, sms: int = 152) -> int:
+def device_bytes(n: int, n_nodes: int, paths: int, sms: int = 152, chunk: int = 0) -> int:
     """Device memory of one request's plan: tables, work-item slots, node
-    outputs, mesh, edge coefficients (FP64 + FP32) and the CG workspace."""
-    chunk = auto_chunk_host(paths, max(n_nodes, 1), sms)
+    outputs, mesh, edge coefficients (FP64 + FP32), the CG workspace (44 B
+    per grid node) and the multigrid levels (at most 15 floats per coarse
+    node: under a third of the grid plus padding rings, bounded by 24 B per
+    grid node) (chunk: the work-item size, 0 = the library's automatic one)."""
+    chunk = chunk or auto_chunk_host(paths, max(n_nodes, 1), sms)
     items = n_nodes * ((paths + chunk - 1) // chunk)
     return (8 * n_nodes + 64 * n + items * SLOT_BYTES + n_nodes * (96 + 32)
-            + 16 * n * n + 24 * n * (n - 1) + 36 * n * n + 4096)
+            + 16 * n * n + 24 * n * (n - 1) + (44 + 24) * n * n + 4096)
 
 
 @dataclass
@@ -107,10 +114,13 @@ class Server:
     def __init__(self, hbm_budget: float = 150e9, n_streams: int = 3, max_batch: int = 256,
                  target_stderr: float | None = 1e-3, pilot_paths: int = 1024,
                  min_paths: int = 1024, max_paths: int = 4_000_000, use_graph: bool = False,
-                 max_wait: float = 0.25, backend=None, cuda=None, sms: int | None = None):
+                 max_wait: float = 0.25, backend=None, cuda=None, sms: int | None = None,
+                 reuse_pilot: bool = True):
         """backend / cuda: the library binding and the stream/event provider
         (default: paper_1310_3435_gb300.native and torch.cuda); tests of the
-        host logic pass stand-ins."""
+        host logic pass stand-ins.  reuse_pilot: the final run continues the
+        pilot's paths (both then use work items of pilot_paths paths, which
+        must be a multiple of 32 up to 8192)."""
         self.N = backend if backend is not None else N
         if cuda is None:
             import torch
@@ -121,7 +131,11 @@ class Server:
         self.max_batch = max_batch
         self.target = target_stderr
         self.pilot_paths = pilot_paths
-        self.min_paths = min_paths
+        self.reuse_pilot = bool(reuse_pilot and target_stderr)
+        if self.reuse_pilot and (pilot_paths % 32 or not 32 <= pilot_paths <= 8192):
+            raise ValueError("reusing the pilot needs pilot_paths a multiple of 32 up to 8192")
+        self.chunk = pilot_paths if self.reuse_pilot else 0
+        self.min_paths = max(min_paths, pilot_paths) if self.reuse_pilot else min_paths
         self.max_paths = max_paths
         self.use_graph = use_graph
         self.max_wait = max_wait
@@ -174,7 +188,7 @@ class Server:
                 req = pending[0]
                 base = device_bytes(req.spec.n, req.spec.n_interface_nodes(),
                                     self.pilot_paths if self.target else int(req.spec.paths),
-                                    self.sms)
+                                    self.sms, self.chunk)
                 if self.used + base > self.budget and (piloting or ready or inflight):
                     break                                   # wait for memory to free up
                 pending.popleft()
@@ -192,7 +206,8 @@ class Server:
                 ev = None
                 if self.target:
                     try:
-                        N.sdd_interface_mc(plan.handle, plan.mc_params(paths=self.pilot_paths),
+                        N.sdd_interface_mc(plan.handle,
+                                           plan.mc_params(paths=self.pilot_paths, chunk=self.chunk),
                                            want_stats=False, stream=self.pilot_stream)
                     except Exception as e:
                         plan.close()
@@ -214,7 +229,7 @@ class Server:
                     self.used -= base
                     results.append(self._dropped(req, "failed", str(e), now()))
                     continue
-                nbytes = device_bytes(req.spec.n, plan.n_nodes, paths, self.sms)
+                nbytes = device_bytes(req.spec.n, plan.n_nodes, paths, self.sms, self.chunk)
                 self.used += nbytes - base
                 self.peak_used = max(self.peak_used, self.used)
                 ready.append([req, plan, paths, nbytes, ta])
@@ -241,7 +256,11 @@ class Server:
             if ready and free_streams and fill:
                 take = [ready.popleft() for _ in range(min(self.max_batch, len(ready)))]
                 plans = [x[1] for x in take]
-                mcs = [p.mc_params(paths=x[2]) for p, x in zip(plans, take)]
+                if self.reuse_pilot:              # continue each request's pilot
+                    mcs = [p.mc_params(paths=x[2], chunk=self.chunk, path_begin=self.pilot_paths)
+                           for p, x in zip(plans, take)]
+                else:
+                    mcs = [p.mc_params(paths=x[2]) for p, x in zip(plans, take)]
                 si = free_streams.popleft()
                 stream = self.streams[si]
                 started = now()

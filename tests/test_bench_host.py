@@ -32,6 +32,13 @@ def test_operation_counts():
 
 
 def test_traffic_is_reported_only_for_its_workload_and_kernel_source(monkeypatch):
+    import hashlib
+    import os
+    src = os.path.join(bench.ROOT, "paper_1310_3435_gb300", "csrc", "mc.cu")
+    with open(src, "rb") as fh:
+        current = hashlib.sha256(fh.read()).hexdigest()
+    # a figure recorded on the current source is reported for its workload
+    monkeypatch.setitem(bench.PATH_KERNEL_TRAFFIC, "source_sha256", current)
     spec = bench.bench_spec(_args())
     assert bench.path_kernel_traffic(spec) == bench.PATH_KERNEL_TRAFFIC["bytes"]
     # another workload, or another kernel source: no figure

@@ -51,6 +51,10 @@ def test_fp64_exponential_matches_oracle(orc, case, exit_test):
     mg, _ = gpu_means(g, n, nodes, nt=True)
     mo, _ = orc.mc_estimate(nodes, n, o["S_nt"], o["Q_nt"], o["paths"] - o["ties"])
     rel = np.abs(mg - mo) / np.maximum(np.abs(mo), 1e-300)
+    # how many node components miss the constant-step bar of 1e-12 (reported,
+    # not asserted: the bar here is REL_EXPO, see above)
+    print("exponential parity %s: %d of %d node components above 1e-12 relative (max %.2e)"
+          % (spec.label, int((rel > 1e-12).sum()), rel.size, float(rel.max())))
     assert rel.max() <= REL_EXPO, rel.max()
     # the random steps are not the constant ones
     g_euler = gpu_sums(replace(spec, stepper=W.STEP_EULER))

@@ -1,6 +1,7 @@
 """Continuous-batching server: requests arriving while others run are
 admitted, batched and overlapped on the device, and every result is bitwise
-the same as the same request run alone."""
+the same as the same request run alone: one run of all its paths, the
+pilot's included (the server's final run continues the pilot's)."""
 import numpy as np
 import pytest
 
@@ -9,14 +10,15 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _alone(spec, paths):
+def _alone(spec, paths, chunk):
+    """One run of all `paths` paths (the work-item size the server used)."""
     from paper_1310_3435_gb300 import native as N
     with N.Plan(spec) as P:
         mesh = np.zeros((spec.n, spec.n, 2))
         mean = np.zeros((P.n_nodes, 2))
         se = np.zeros((P.n_nodes, 2))
-        N.sdd_mesh_generate(P.handle, P.mc_params(paths=paths), P.solve_params(), mesh, mean, se,
-                            allow_not_converged=True)
+        N.sdd_mesh_generate(P.handle, P.mc_params(paths=paths, chunk=chunk), P.solve_params(),
+                            mesh, mean, se, allow_not_converged=True)
         return mesh, mean, se
 
 
@@ -31,7 +33,7 @@ def test_served_results_equal_alone():
     assert srv.launches >= 3                         # several batches, some overlapping
     for r in res:
         assert r.max_stderr <= 4e-3 * 1.25           # pilot-chosen N meets the target
-        mesh, mean, se = _alone(r.spec, r.paths)
+        mesh, mean, se = _alone(r.spec, r.paths, srv.chunk)    # pilot paths included
         assert np.array_equal(r.mean, mean), r.rid
         assert np.array_equal(r.stderr, se), r.rid
         assert np.array_equal(r.mesh, mesh), r.rid

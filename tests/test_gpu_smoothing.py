@@ -1,5 +1,5 @@
-"""The fully probabilistic mesh (§3.4: Monte Carlo at every interior node)
-and Perona-Malik smoothing (§3.5) on the GPU, against the oracle."""
+"""The fully probabilistic mesh (§3.3: Monte Carlo at every interior node)
+and Perona-Malik smoothing (§3.4) on the GPU, against the oracle."""
 from dataclasses import replace
 
 import numpy as np
@@ -123,7 +123,7 @@ def test_fully_probabilistic_mesh_matches_oracle(orc):
 
 
 def test_smoothing_improves_a_noisy_probabilistic_mesh(orc):
-    """The paper's observation (§3.5): a few Perona-Malik steps bring the
+    """The paper's observation (§3.4): a few Perona-Malik steps bring the
     quality of a low-N fully probabilistic mesh of the running example
     towards the deterministic mesh's."""
     import math

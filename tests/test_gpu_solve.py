@@ -32,7 +32,8 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("solver", [W.SOLVER_SOR, W.SOLVER_CG_FP32_REFINE])
+@pytest.mark.parametrize("solver", [W.SOLVER_SOR, W.SOLVER_CG_FP32_REFINE,
+                                    W.SOLVER_CG_JACOBI_FP32_REFINE])
 def test_domain_decomposition_exactness(orc, case, solver):
     """Interface data from the oracle's single-domain mesh: the GPU stitched
     mesh reproduces that mesh (non-iterative DD is exact with exact data)."""
@@ -46,7 +47,8 @@ def test_domain_decomposition_exactness(orc, case, solver):
     assert np.max(np.abs(mesh - G)) <= MESH_TOL
 
 
-@pytest.mark.parametrize("solver", [W.SOLVER_SOR, W.SOLVER_CG_FP32_REFINE])
+@pytest.mark.parametrize("solver", [W.SOLVER_SOR, W.SOLVER_CG_FP32_REFINE,
+                                    W.SOLVER_CG_JACOBI_FP32_REFINE])
 def test_solve_matches_oracle_with_noisy_interface(orc, solver):
     """Interface values with Monte Carlo-like noise: the stitched meshes of
     both sides agree (the solve is linear in the Dirichlet data)."""
@@ -60,13 +62,36 @@ def test_solve_matches_oracle_with_noisy_interface(orc, solver):
     assert np.max(np.abs(mesh - ref)) <= MESH_TOL
 
 
+def test_multigrid_preconditioner_cuts_the_iterations(orc):
+    """197 x 197 split 2 x 2 (97 x 97 interior nodes per subdomain, the
+    paper's four-subdomain case, where the solves dominate): the multigrid-
+    preconditioned CG needs a few dozen iterations in all, the diagonally
+    preconditioned one hundreds; both match the oracle's stitched mesh."""
+    spec = W.MeshSpec(n=197, sx=2, sy=2, family=W.FAMILY_RING,
+                      params=(10.0, 0.5, 0.5, 50.0, 0.25))
+    nodes = orc.interface_nodes(spec.n, spec.sx, spec.sy)
+    rng = np.random.default_rng(5)
+    iface = nodes / (spec.n - 1.0) + rng.normal(0, 2e-3, size=nodes.shape)
+    ref = orc.stitch(spec.n, spec.sx, spec.sy, oracle_edges(orc, spec), iface, spec.family,
+                     spec.coef_mode, spec.params)
+    mesh_mg, st_mg = _solve(spec, iface, W.SOLVER_CG_FP32_REFINE, 1e-13)
+    mesh_j, st_j = _solve(spec, iface, W.SOLVER_CG_JACOBI_FP32_REFINE, 1e-13)
+    assert st_mg.converged == st_j.converged == 4
+    assert st_mg.max_iterations <= 60, st_mg.max_iterations
+    assert st_j.max_iterations >= 5 * st_mg.max_iterations, (st_j.max_iterations,
+                                                            st_mg.max_iterations)
+    assert st_mg.node_iterations <= 4 * 97 * 97 * st_mg.max_iterations
+    assert np.max(np.abs(mesh_mg - ref)) <= MESH_TOL
+    assert np.max(np.abs(mesh_j - ref)) <= MESH_TOL
+
+
 def test_solver_tolerance_and_stats(orc):
     spec = CASES[3]
     nodes = orc.interface_nodes(spec.n, spec.sx, spec.sy)
     E = oracle_edges(orc, spec)
     G = orc.global_solve(spec.n, E, spec.family, spec.coef_mode, spec.params)
     iface = G[nodes[:, 1], nodes[:, 0], :]
-    for solver in (W.SOLVER_SOR, W.SOLVER_CG_FP32_REFINE):
+    for solver in (W.SOLVER_SOR, W.SOLVER_CG_FP32_REFINE, W.SOLVER_CG_JACOBI_FP32_REFINE):
         mesh, st = _solve(spec, iface, solver, 1e-10)
         assert st.converged == st.subdomains == 4
         assert st.max_rel_residual <= 1e-10

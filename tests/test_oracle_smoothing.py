@@ -1,4 +1,4 @@
-"""Pins of the oracle's Perona-Malik mesh smoothing (§3.5, eq.
+"""Pins of the oracle's Perona-Malik mesh smoothing (§3.4, eq.
 PeronaMalikDiffusion, FTCS): the heat-equation limit against the exact decay
 of a discrete eigenfunction, fixed points, edge preservation, conservation
 and the maximum principle."""

@@ -31,7 +31,7 @@ BMAP_IDENTITY, BMAP_PAPER_1D, BMAP_TABLE = 0, 1, 2
 FP64, FP32_STEP = 0, 1
 EXIT_END_OF_STEP, EXIT_BRIDGE = 0, 1
 STEP_EULER, STEP_EXPONENTIAL = 0, 1
-SOLVER_SOR, SOLVER_CG_FP32_REFINE = 0, 1
+SOLVER_SOR, SOLVER_CG_FP32_REFINE, SOLVER_CG_JACOBI_FP32_REFINE = 0, 1, 2
 
 
 @dataclass(frozen=True)
