@@ -77,15 +77,17 @@ def env_rank():
 # capture of the timed launch (dram__bytes_read.sum + dram__bytes_write.sum).
 # Valid only for the kernel source it was taken on: the bench line reports
 # null traffic once the source's SHA-256 differs.
-PATH_KERNEL_TRAFFIC = {"bytes": 1104128 + 1055744,
-                       "source_sha256": "4d2080faba5d65e441f327e48f3f4458f95dfcea13341faed31fc463c92d7dad"}
+PATH_KERNEL_TRAFFIC = {"bytes": 900352 + 1052672,
+                       "source_sha256": "c24e2b39ed27fb55b4cebabef86d94b3304c15ab0dbff1d7611f2fa04c113061"}
 
 
-# Pipe and issue activity of the same kernel from one `ncu --section
-# ComputeWorkloadAnalysis` capture (sm__inst_executed_pipe_fma / fmaheavy
-# cycles over elapsed cycles, and the issue-slot activity), keyed to the
-# kernel source like the traffic: null once the source changes.
-PATH_KERNEL_COUNTERS = {"fp32_fma_pipe": None, "issue_active": None, "source_sha256": ""}
+# FP32 (FMA) pipe and issue-slot activity of the same kernel, from one ncu
+# capture of the bench workload at N = 16384 (the same kernel, launch shape and
+# chunking; sm__inst_executed_pipe_fma and smsp__issue_active, each as a share
+# of its peak over the active cycles), keyed to the kernel source like the
+# traffic: null once the source changes.
+PATH_KERNEL_COUNTERS = {"fp32_fma_pipe": 0.3705, "issue_active": 0.7543,
+                        "source_sha256": "c24e2b39ed27fb55b4cebabef86d94b3304c15ab0dbff1d7611f2fa04c113061"}
 
 
 def _mc_source_digest():
@@ -447,10 +449,10 @@ def run_native(args):
         # plain FP64 against mixed precision on one smaller stream (FP64 stepping
         # runs about 300x fewer path-steps/s): the same requests, both precisions
         small = dict(rates=[args.fp64_served_rate], count=args.fp64_served_count,
-                     target_stderr=args.served_stderr, n_max=129)
+                     target_stderr=args.served_stderr, n_max=97)
         line["served_fp64"] = {"fp64": serve_leg(precision=W.FP64, **small),
                                "fp32_step_same_stream": serve_leg(precision=W.FP32_STEP, **small),
-                               "note": "scaled down to n <= 129 so that FP64 stepping keeps up"}
+                               "note": "scaled down to n <= 97 so that FP64 stepping keeps up"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -1060,7 +1062,7 @@ def batched_leg(N, count=256, paths=0, autotune=True, steps=1, warmup=1, stream=
 
 
 def serve_leg(rates, count, target_stderr, n_max, precision=W.FP32_STEP, max_batch=64,
-              reuse_pilot=True, seed=0):
+              reuse_pilot=True, seed=0, **server_kw):
     """Serving runs: a Poisson stream of `count` mesh requests per rate (n
     log-uniform 65..n_max, splits 2..8, 1-3 bumps, dt = 5e-5), paths per node
     from a 1024-path pilot for the std-err target, continuous batching;
@@ -1072,15 +1074,18 @@ def serve_leg(rates, count, target_stderr, n_max, precision=W.FP32_STEP, max_bat
         arr = W.config5(count=count, rate=rate, seed=seed, n_max=n_max)
         reqs = [S.Request(i, W.MeshSpec(**{**a.spec.__dict__, "precision": precision}), a.t)
                 for i, a in enumerate(arr)]
-        srv = S.Server(hbm_budget=150e9, n_streams=3, max_batch=max_batch,
-                       target_stderr=target_stderr, reuse_pilot=reuse_pilot)
+        kw = dict(hbm_budget=150e9, n_streams=3, max_batch=max_batch,
+                  target_stderr=target_stderr, reuse_pilot=reuse_pilot)
+        kw.update(server_kw)
+        srv = S.Server(**kw)
         t0 = time.perf_counter()
         res = srv.run(reqs)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         summ = S.summarize(res)
         summ.update({"rate_req_s": rate, "wall_s": wall, "batches_launched": srv.launches,
-                     "peak_budget_bytes": srv.peak_used})
+                     "peak_budget_bytes": srv.peak_used,
+                     "device_busy": S.busy_fraction(srv.trace)})
         out.append(summ)
     return {"workload": "Poisson stream, n log-uniform 65..%d, splits 2..8, 1-3 bumps, dt=5e-5, "
                         "std-err target %g (paths per node from a 1024-path pilot%s), %s stepping"
@@ -1135,8 +1140,8 @@ def main(argv=None):
     ap.add_argument("--served-rates", type=float, nargs="+", default=[4.0, 16.0])
     ap.add_argument("--served-count", type=int, default=200)
     ap.add_argument("--served-stderr", type=float, default=5e-3)
-    ap.add_argument("--fp64-served-rate", type=float, default=0.5)
-    ap.add_argument("--fp64-served-count", type=int, default=24)
+    ap.add_argument("--fp64-served-rate", type=float, default=0.3)
+    ap.add_argument("--fp64-served-count", type=int, default=12)
     ap.add_argument("--chunk", type=int, default=0, help="paths per work item (0: automatic)")
     ap.add_argument("--paths", type=int, default=0,
                     help="override paths per node (profiling runs on a small case)")

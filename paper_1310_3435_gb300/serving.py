@@ -146,6 +146,9 @@ class Server:
         self.peak_used = 0
         self.launches = 0
         self._cancel = set()
+        # timeline of the last run (seconds after its start): ("pilot", rid,
+        # queued, seen done) and ("batch", id, launched, seen done, requests)
+        self.trace = []
 
     def cancel(self, rid: int) -> None:
         """Cancels request `rid`: a request not yet in a batch is dropped at
@@ -180,6 +183,7 @@ class Server:
         bid = 0
         t0 = time.perf_counter()
         now = lambda: (time.perf_counter() - t0) * time_scale
+        self.trace = []
         while pending or piloting or ready or inflight:
             progressed = False
             t = now()
@@ -221,6 +225,7 @@ class Server:
             while piloting and (piloting[0][2] is None or piloting[0][2].query()):
                 req, plan, ev, base, ta = piloting.popleft()
                 progressed = True
+                self.trace.append(("pilot", req.rid, ta, now()))
                 try:
                     st = N.sdd_plan_last_mc_stats(plan.handle) if ev is not None else None
                     paths = self._paths_for(req.spec, st)
@@ -294,6 +299,7 @@ class Server:
             for f in inflight:
                 if f.event.query():
                     done = now()
+                    self.trace.append(("batch", f.bid, f.started, done, len(f.reqs)))
                     for k, (req, plan) in enumerate(zip(f.reqs, f.plans)):
                         admitted = getattr(req, "admitted_at", f.started)
                         if req.rid in self._cancel:
@@ -333,6 +339,24 @@ class Server:
                 else:
                     time.sleep(poll_sleep)
         return results
+
+
+def busy_fraction(trace, span=None) -> float:
+    """Share of the run during which at least one batch or pilot was on the
+    device (union of their intervals in the trace, as the host saw them)."""
+    iv = sorted((e[2], e[3]) for e in trace)
+    if not iv:
+        return 0.0
+    total, cur_s, cur_e = 0.0, iv[0][0], iv[0][1]
+    for a, b in iv[1:]:
+        if a > cur_e:
+            total += cur_e - cur_s
+            cur_s, cur_e = a, b
+        else:
+            cur_e = max(cur_e, b)
+    total += cur_e - cur_s
+    span = span if span is not None else max(e[3] for e in trace) - min(e[2] for e in trace)
+    return total / span if span > 0 else 0.0
 
 
 def summarize(results, wall: float | None = None) -> dict:

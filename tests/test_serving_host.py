@@ -222,3 +222,10 @@ def test_cancelled_requests():
     assert by[last].status == "cancelled" and by[last].mesh is None
     assert all(r.status == "ok" for k, r in by.items() if k not in (5, last))
     assert srv.used == 0 and lib.live_plans == 0
+
+
+def test_busy_fraction_is_the_union_of_device_intervals():
+    trace = [("pilot", 0, 0.0, 1.0), ("batch", 0, 0.5, 2.0, 3), ("batch", 1, 3.0, 4.0, 1)]
+    assert S.busy_fraction(trace) == pytest.approx(3.0 / 4.0)
+    assert S.busy_fraction([]) == 0.0
+    assert S.busy_fraction(trace, span=6.0) == pytest.approx(0.5)
