@@ -445,7 +445,7 @@ def run_native(args):
         line["batched"] = batched_leg(N, count=args.count)
     if rank == 0 and not args.no_served:
         line["served"] = serve_leg(args.served_rates, args.served_count, args.served_stderr,
-                                   1025, precision=W.FP32_STEP)
+                                   1025, precision=W.FP32_STEP, ideal=True)
         # plain FP64 against mixed precision on one smaller stream (FP64 stepping
         # runs about 300x fewer path-steps/s): the same requests, both precisions
         small = dict(rates=[args.fp64_served_rate], count=args.fp64_served_count,
@@ -909,6 +909,32 @@ def precision_bias_leg(N, spec, sample, timed_max_stderr, stream):
                     "precision-induced bias; the timed result's Monte Carlo std-err beside it"}
 
 
+def bias_on_sample(N, specs, nodes_per_mesh=8, paths=2048):
+    """Precision-induced bias of FP32 stepping on a sample: for each mesh, evenly
+    spaced interface nodes, the first `paths` paths of each on the GPU (the
+    timed precision) and in the FP64 oracle, the same Philox streams."""
+    import oracle
+    worst, worst_sigma, signed, count = 0.0, 0.0, 0.0, 0
+    for spec in specs:
+        sub = W.MeshSpec(**{**spec.__dict__, "paths": paths})
+        nodes = oracle.interface_nodes(sub.n, sub.sx, sub.sy)
+        idx = np.linspace(0, len(nodes) - 1, min(nodes_per_mesh, len(nodes))).round().astype(int)
+        with N.Plan(sub) as P:
+            g = N.sdd_interface_mc_sums(P.handle, P.mc_params())
+        E = oracle.bmap_tables(sub.n, sub.bmap_mode, sub.family, sub.coef_mode, sub.params)
+        o = oracle.mc_nodes(sub.n, nodes[idx], E, sub.family, sub.coef_mode, sub.params, sub.seed,
+                            paths, sub.dt, sub.cap(), 1e-11, node_ids=idx,
+                            exit_test=sub.exit_test, stepper=sub.stepper)
+        d = (g["sum"][idx] - o["S_all"]) / float(paths)
+        se = np.sqrt(np.maximum(o["Q_all"] - o["S_all"] ** 2 / paths, 0) / (paths * (paths - 1.0)))
+        worst = max(worst, float(np.abs(d).max()))
+        worst_sigma = max(worst_sigma, float((np.abs(d) / np.maximum(se, 1e-300)).max()))
+        signed += float(d.sum())
+        count += d.size
+    return {"sample": "%d meshes x %d nodes x first %d paths" % (len(specs), nodes_per_mesh, paths),
+            "max_abs": worst, "max_abs_over_stderr": worst_sigma, "mean_signed": signed / count}
+
+
 def mesh_quality_of(N, plan, mesh):
     """Q_max, Q_mean and folded cells of a generated mesh (k_quality)."""
     q = N.sdd_mesh_quality(plan.handle, mesh)
@@ -1048,6 +1074,7 @@ def batched_leg(N, count=256, paths=0, autotune=True, steps=1, warmup=1, stream=
                               "note": "multigrid-preconditioned FP32 CG: algorithmic bytes of "
                                       "level 0 per interior node and iteration x the nodes and "
                                       "iterations the solves ran, over the fill + solve phase"},
+           "precision_bias": bias_on_sample(N, [specs[0], specs[len(specs) // 2]]),
            "jacobi_pcg": {"ms_fill_and_solves": ms_jac, "solve_max_iterations": its_jac,
                           "node_iterations": node_its_jac, "solves_converged": ok_jac,
                           "note": "the same solves with the diagonal preconditioner"},
@@ -1062,14 +1089,18 @@ def batched_leg(N, count=256, paths=0, autotune=True, steps=1, warmup=1, stream=
 
 
 def serve_leg(rates, count, target_stderr, n_max, precision=W.FP32_STEP, max_batch=64,
-              reuse_pilot=True, seed=0, **server_kw):
+              reuse_pilot=True, seed=0, ideal=False, **server_kw):
     """Serving runs: a Poisson stream of `count` mesh requests per rate (n
     log-uniform 65..n_max, splits 2..8, 1-3 bumps, dt = 5e-5), paths per node
     from a 1024-path pilot for the std-err target, continuous batching;
-    p50/p99 latency and meshes/s per rate."""
+    p50/p99 latency and meshes/s per rate.  ideal: also the same requests of
+    the last rate, at the paths per node the server chose, as one batch (the
+    rate the path kernels reach on these meshes without arrivals or pilots)."""
     import torch
+    from paper_1310_3435_gb300 import native as N
     from paper_1310_3435_gb300 import serving as S
     out = []
+    res = []
     for rate in rates:
         arr = W.config5(count=count, rate=rate, seed=seed, n_max=n_max)
         reqs = [S.Request(i, W.MeshSpec(**{**a.spec.__dict__, "precision": precision}), a.t)
@@ -1082,16 +1113,42 @@ def serve_leg(rates, count, target_stderr, n_max, precision=W.FP32_STEP, max_bat
         res = srv.run(reqs)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        del reqs
         summ = S.summarize(res)
         summ.update({"rate_req_s": rate, "wall_s": wall, "batches_launched": srv.launches,
                      "peak_budget_bytes": srv.peak_used,
                      "device_busy": S.busy_fraction(srv.trace)})
         out.append(summ)
+    ideal_line = None
+    if ideal and res:
+        paths = {r.rid: r.paths for r in res if r.status == "ok"}
+        specs = [r.spec for r in sorted(res, key=lambda r: r.rid) if r.rid in paths]
+        plans = [N.Plan(sp) for sp in specs]
+        chunk = 1024 if reuse_pilot else 0
+        mcs = [p.mc_params(paths=paths[r], chunk=chunk)
+               for p, r in zip(plans, sorted(paths))]
+        stream = torch.cuda.Stream()
+        with N.Batch(plans, mcs, [p.solve_params() for p in plans]) as B:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.run(stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1000.0
+            steps = sum(int(B.stats(i, allow_not_converged=True)[0].path_steps)
+                        for i in range(len(plans)))
+        for p in plans:
+            p.close()
+        ideal_line = {"requests": len(plans), "seconds": sec, "path_steps_per_s": steps / sec,
+                      "meshes_per_s": len(plans) / sec,
+                      "served_over_ideal": out[-1]["path_steps_per_s"] / (steps / sec),
+                      "note": "the last rate's requests at the served paths per node as one "
+                              "batch: the rate the kernels reach on these meshes"}
     return {"workload": "Poisson stream, n log-uniform 65..%d, splits 2..8, 1-3 bumps, dt=5e-5, "
                         "std-err target %g (paths per node from a 1024-path pilot%s), %s stepping"
                         % (n_max, target_stderr, ", continued by the final run" if reuse_pilot else "",
                            "FP32" if precision == W.FP32_STEP else "FP64"),
-            "requests_per_rate": count, "rates": out}
+            "requests_per_rate": count, "rates": out, "ideal_batch": ideal_line}
 
 
 def main(argv=None):

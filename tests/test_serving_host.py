@@ -59,6 +59,7 @@ class FakeLib:
         self.batches = []
         self.concurrent = 0
         self.max_concurrent = 0
+        self.final_mcs = []
 
     class _Plan:
         def __init__(self, lib, spec):
@@ -70,7 +71,8 @@ class FakeLib:
             self.pilot_paths = None
 
         def mc_params(self, **kw):
-            return dict(paths=kw.get("paths", self.spec.paths))
+            return dict(paths=kw.get("paths", self.spec.paths), chunk=kw.get("chunk", 0),
+                        path_begin=kw.get("path_begin", 0))
 
         def solve_params(self):
             return {}
@@ -85,6 +87,7 @@ class FakeLib:
 
     def sdd_interface_mc(self, handle, mc, want_stats=False, stream=None):
         handle.pilot_paths = mc["paths"]
+        handle.pilot_chunk = mc["chunk"]
         stream.enqueue(0.001)
 
     def sdd_plan_last_mc_stats(self, handle):
@@ -94,6 +97,7 @@ class FakeLib:
         def __init__(self, lib, plans, mcs, sps):
             self.lib, self.plans, self.mcs = lib, plans, mcs
             lib.batches.append([m["paths"] for m in mcs])
+            lib.final_mcs.extend((p, m) for p, m in zip(plans, mcs))
 
         def run(self, use_graph=False, stream=None):
             stream.enqueue(0.002 * len(self.plans))
@@ -229,3 +233,26 @@ def test_busy_fraction_is_the_union_of_device_intervals():
     assert S.busy_fraction(trace) == pytest.approx(3.0 / 4.0)
     assert S.busy_fraction([]) == 0.0
     assert S.busy_fraction(trace, span=6.0) == pytest.approx(0.5)
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_final_runs_continue_the_pilots(reuse):
+    """With reuse the final run of every request continues its pilot: the
+    same work-item size for both (the pilot's path count) and path_begin =
+    pilot paths, so the pilot's paths count in the estimate; without it the
+    final run starts at path 0."""
+    lib = FakeLib()
+    srv = S.Server(hbm_budget=1e12, n_streams=2, max_batch=4, target_stderr=1e-3,
+                   pilot_paths=512, min_paths=256, backend=lib, cuda=FakeCuda, sms=152,
+                   reuse_pilot=reuse)
+    res = srv.run(_requests(10, rate=3000.0))
+    assert len(res) == 10 and len(lib.final_mcs) == 10
+    for plan, mc in lib.final_mcs:
+        if reuse:
+            assert mc["path_begin"] == 512 and mc["chunk"] == 512
+            assert plan.pilot_chunk == 512 and mc["paths"] >= 512
+        else:
+            assert mc["path_begin"] == 0 and mc["chunk"] == 0 and plan.pilot_chunk == 0
+    with pytest.raises(ValueError):
+        S.Server(target_stderr=1e-3, pilot_paths=1000, backend=lib, cuda=FakeCuda, sms=152)
+
