@@ -47,6 +47,24 @@ def test_bridge_rule_cases(orc):
     assert abs(hits / 20000 - p) < 4 * math.sqrt(p * (1 - p) / 20000)
 
 
+def test_bridge_near_a_corner_tests_each_side_with_its_own_chance(orc):
+    """Near the corner (0, 0) two sides can be crossed.  Side s = 0 is tested
+    first, then, if it was not crossed, t = 0, each with its own uniform: the
+    frequencies must be p_s and (1 - p_s) p_t (one uniform for both sides
+    would give max(0, p_t - p_s) for t = 0)."""
+    dt = 1e-4
+    xs, ys, xt, yt = 0.004, 0.006, 0.003, 0.005
+    ps, pt = math.exp(-xs * ys / dt), math.exp(-xt * yt / dt)
+    K = 40000
+    edges = [orc.bridge_exit(xs, xt, ys, yt, dt, 5, 1, q, 13)[0] for q in range(K)]
+    fs = edges.count(2) / K                          # side s = 0 is edge 2
+    ft = edges.count(0) / K                          # side t = 0 is edge 0
+    want_t = (1 - ps) * pt
+    assert abs(fs - ps) < 4 * math.sqrt(ps * (1 - ps) / K), (fs, ps)
+    assert abs(ft - want_t) < 4 * math.sqrt(want_t * (1 - want_t) / K), (ft, want_t)
+    assert abs(ft - max(0.0, pt - ps)) > 10 * math.sqrt(want_t / K)   # the two rules differ here
+
+
 def _tau(orc, s0, t0, dt, N, exit_test, seed=9):
     E = orc.bmap_tables(5, W.BMAP_IDENTITY)
     r = orc.mc_nodes(5, [(int(round(s0 * 4)), int(round(t0 * 4)))], E, W.FAMILY_BUMPS, W.COEF_W,
