@@ -405,8 +405,9 @@ __device__ __forceinline__ int nearest_edge(R s, R t, R& tau)
 // uniforms are drawn.  Returns the edge and the tangential coordinate of the
 // exit point (mean of the step's two), or -1.
 template <typename R, class Keys>
-__device__ __noinline__ int bridge_exit(R xs, R xt, R ys, R yt, R inv_dt, R qmax, const Keys& philox,
-                                        uint32_t k, uint32_t path, uint32_t node, R& tau, bool& tie)
+__device__ __forceinline__ int bridge_exit_inl(R xs, R xt, R ys, R yt, R inv_dt, R qmax,
+                                               const Keys& philox, uint32_t k, uint32_t path,
+                                               uint32_t node, R& tau, bool& tie)
 {
     const R q[4] = {xs * ys, (R(1) - xs) * (R(1) - ys), xt * yt, (R(1) - xt) * (R(1) - yt)};
     if (!((q[0] < qmax) | (q[1] < qmax) | (q[2] < qmax) | (q[3] < qmax))) return -1;
@@ -431,6 +432,15 @@ __device__ __noinline__ int bridge_exit(R xs, R xt, R ys, R yt, R inv_dt, R qmax
         }
     }
     return -1;
+}
+
+// The same test as a called function: the FP64 runner and the FP32 kernels
+// without the test keep it out of their register allocation.
+template <typename R, class Keys>
+__device__ __noinline__ int bridge_exit(R xs, R xt, R ys, R yt, R inv_dt, R qmax, const Keys& philox,
+                                        uint32_t k, uint32_t path, uint32_t node, R& tau, bool& tie)
+{
+    return bridge_exit_inl<R>(xs, xt, ys, yt, inv_dt, qmax, philox, k, path, node, tau, tie);
 }
 
 // Linear interpolation in a table of n values at tau_j = j/(n-1), in FP64.
@@ -936,7 +946,7 @@ __device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs
 // Streams the items of mesh M starting at `first` (already taken from the
 // queue).  Returns the first item taken that is not M's (the next mesh's, or
 // >= total_items when the queue is exhausted).
-template <bool EXPO, class Dens, class Keys>
+template <bool EXPO, bool BRIDGE, class Dens, class Keys>
 __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const Dens& dens,
                                                          const Keys& philox,
                                                          unsigned long long first,
@@ -962,7 +972,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
     __syncwarp();
 
     const float c4dt = (float)(-4.0 * M.dt * 0.69314718055994530942);
-    const bool bridge = M.bridge != 0;
+    constexpr bool bridge = BRIDGE;          // the kernel with the test inlines it
     const float inv_dt = (float)(1.0 / M.dt), qmax = (float)(23.0 * M.dt);
     const float dth = (float)std::sqrt(23.0 * M.dt);
     constexpr float LN2F = 0.69314718055994530942f;
@@ -1074,7 +1084,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                 const bool out1 = (y1s <= 0.f) | (y1s >= 1.f) | (y1t <= 0.f) | (y1t >= 1.f);
                 if (out1) {
                     e = exit_edge<float>(xs, xt, y1s, y1t, tau);
-                } else if (bridge && (e = bridge_exit<float>(xs, xt, y1s, y1t,
+                } else if (bridge && (e = bridge_exit_inl<float>(xs, xt, y1s, y1t,
                                                               EXPO ? inv_dt / fa : inv_dt,
                                                               EXPO ? qmax * fa : qmax, philox,
                                                               k - 1u, path, nid, tau, dummy)) >= 0) {
@@ -1086,7 +1096,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
                     const bool out2 = (y2s <= 0.f) | (y2s >= 1.f) | (y2t <= 0.f) | (y2t >= 1.f);
                     if (out2) {
                         e = exit_edge<float>(y1s, y1t, y2s, y2t, tau);
-                    } else if (bridge && (e = bridge_exit<float>(y1s, y1t, y2s, y2t,
+                    } else if (bridge && (e = bridge_exit_inl<float>(y1s, y1t, y2s, y2t,
                                                                   EXPO ? inv_dt / fb : inv_dt,
                                                                   EXPO ? qmax * fb : qmax,
                                                                   philox, k - 1u, path, nid, tau,
@@ -1138,41 +1148,41 @@ __host__ __device__ __forceinline__ int fam_class(int family, int nb)
     return FC_BUMPS6;
 }
 
-template <int FC, bool EXPO, class Keys>
+template <int FC, bool EXPO, bool BRIDGE, class Keys>
 __device__ __forceinline__ unsigned long long stream_fc(const MeshDev& M, const Keys& keys,
                                                         unsigned long long item, const McArgs& a,
                                                         WarpAcc& W, int lane)
 {
-    if constexpr (FC == FC_RING) { RingF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_RIDGE) { RidgeF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_TABLE) { TableF32 d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_BUMPS1) { BumpsF32<1> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_BUMPS2) { BumpsF32<2> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
-    if constexpr (FC == FC_BUMPS3) { BumpsF32<3> d; d.load(M); return run_stream<EXPO>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_RING) { RingF32 d; d.load(M); return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_RIDGE) { RidgeF32 d; d.load(M); return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_TABLE) { TableF32 d; d.load(M); return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS1) { BumpsF32<1> d; d.load(M); return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS2) { BumpsF32<2> d; d.load(M); return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane); }
+    if constexpr (FC == FC_BUMPS3) { BumpsF32<3> d; d.load(M); return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane); }
     if constexpr (FC == FC_BUMPS6) {
         BumpsF32<SDD_MAX_BUMPS> d;
         d.load(M);
-        return run_stream<EXPO>(M, d, keys, item, a, W, lane);
+        return run_stream<EXPO, BRIDGE>(M, d, keys, item, a, W, lane);
     }
     return a.total_items;
 }
 
-template <int FC, bool EXPO, class Keys>
+template <int FC, bool EXPO, bool BRIDGE, class Keys>
 __device__ __forceinline__ unsigned long long dispatch_stream(const MeshDev& M, const Keys& keys,
                                                               unsigned long long item,
                                                               const McArgs& a, WarpAcc& W, int lane)
 {
     if constexpr (FC != FC_ANY) {
-        return stream_fc<FC, EXPO>(M, keys, item, a, W, lane);
+        return stream_fc<FC, EXPO, BRIDGE>(M, keys, item, a, W, lane);
     } else {
         switch (fam_class(M.family, M.nb)) {
-            case FC_RING: return stream_fc<FC_RING, EXPO>(M, keys, item, a, W, lane);
-            case FC_RIDGE: return stream_fc<FC_RIDGE, EXPO>(M, keys, item, a, W, lane);
-            case FC_TABLE: return stream_fc<FC_TABLE, EXPO>(M, keys, item, a, W, lane);
-            case FC_BUMPS1: return stream_fc<FC_BUMPS1, EXPO>(M, keys, item, a, W, lane);
-            case FC_BUMPS2: return stream_fc<FC_BUMPS2, EXPO>(M, keys, item, a, W, lane);
-            case FC_BUMPS3: return stream_fc<FC_BUMPS3, EXPO>(M, keys, item, a, W, lane);
-            default: return stream_fc<FC_BUMPS6, EXPO>(M, keys, item, a, W, lane);
+            case FC_RING: return stream_fc<FC_RING, EXPO, BRIDGE>(M, keys, item, a, W, lane);
+            case FC_RIDGE: return stream_fc<FC_RIDGE, EXPO, BRIDGE>(M, keys, item, a, W, lane);
+            case FC_TABLE: return stream_fc<FC_TABLE, EXPO, BRIDGE>(M, keys, item, a, W, lane);
+            case FC_BUMPS1: return stream_fc<FC_BUMPS1, EXPO, BRIDGE>(M, keys, item, a, W, lane);
+            case FC_BUMPS2: return stream_fc<FC_BUMPS2, EXPO, BRIDGE>(M, keys, item, a, W, lane);
+            case FC_BUMPS3: return stream_fc<FC_BUMPS3, EXPO, BRIDGE>(M, keys, item, a, W, lane);
+            default: return stream_fc<FC_BUMPS6, EXPO, BRIDGE>(M, keys, item, a, W, lane);
         }
     }
 }
@@ -1212,7 +1222,7 @@ struct PathShape {
                                       : kNarrow ? 7 : SDD_MC_MIN_BLOCKS_F32;
 };
 
-template <int PREC, bool ONE, int FC, bool EXPO = false>
+template <int PREC, bool ONE, int FC, bool EXPO = false, bool BRIDGE = false>
 __global__ void __launch_bounds__(PathShape<PREC, ONE, FC, EXPO>::threads,
                                   PathShape<PREC, ONE, FC, EXPO>::min_blocks)
 k_paths(const __grid_constant__ McArgs a)
@@ -1262,7 +1272,7 @@ k_paths(const __grid_constant__ McArgs a)
             const MeshDev& M = ONE ? single : a.meshes[find_mesh(a.item_off, a.n_meshes, item)];
             if constexpr (ONE) {
                 const ParamKeys keys{a.rk};
-                item = dispatch_stream<FC, EXPO>(M, keys, item, a, W, lane);
+                item = dispatch_stream<FC, EXPO, BRIDGE>(M, keys, item, a, W, lane);
             } else {
                 __syncwarp();
                 if (lane < 20) {
@@ -1272,7 +1282,7 @@ k_paths(const __grid_constant__ McArgs a)
                 }
                 __syncwarp();
                 const SmemKeys keys{wkeys[tid >> 5]};
-                item = dispatch_stream<FC, EXPO>(M, keys, item, a, W, lane);
+                item = dispatch_stream<FC, EXPO, BRIDGE>(M, keys, item, a, W, lane);
             }
         }
     }
@@ -1431,32 +1441,33 @@ void fill_fp32_params(MeshDev& m, const sdd_density& d)
 }
 
 // Kernel of a launch: precision, single mesh or batch, kernel class (density
-// class + KC_EXPO for exponential time stepping).
+// class + KC_EXPO for exponential time stepping + KC_BRIDGE for the
+// Brownian-bridge test).
 using PathKernel = void (*)(McArgs);
 
-template <bool EXPO>
+template <bool EXPO, bool BRIDGE>
 static PathKernel path_kernel_fp32(bool one, int fc)
 {
     if (!one) {
         switch (fc) {
-            case FC_RING: return k_paths<SDD_FP32_STEP, false, FC_RING, EXPO>;
-            case FC_RIDGE: return k_paths<SDD_FP32_STEP, false, FC_RIDGE, EXPO>;
-            case FC_TABLE: return k_paths<SDD_FP32_STEP, false, FC_TABLE, EXPO>;
-            case FC_BUMPS1: return k_paths<SDD_FP32_STEP, false, FC_BUMPS1, EXPO>;
-            case FC_BUMPS2: return k_paths<SDD_FP32_STEP, false, FC_BUMPS2, EXPO>;
-            case FC_BUMPS3: return k_paths<SDD_FP32_STEP, false, FC_BUMPS3, EXPO>;
-            case FC_BUMPS6: return k_paths<SDD_FP32_STEP, false, FC_BUMPS6, EXPO>;
-            default: return k_paths<SDD_FP32_STEP, false, FC_ANY, EXPO>;
+            case FC_RING: return k_paths<SDD_FP32_STEP, false, FC_RING, EXPO, BRIDGE>;
+            case FC_RIDGE: return k_paths<SDD_FP32_STEP, false, FC_RIDGE, EXPO, BRIDGE>;
+            case FC_TABLE: return k_paths<SDD_FP32_STEP, false, FC_TABLE, EXPO, BRIDGE>;
+            case FC_BUMPS1: return k_paths<SDD_FP32_STEP, false, FC_BUMPS1, EXPO, BRIDGE>;
+            case FC_BUMPS2: return k_paths<SDD_FP32_STEP, false, FC_BUMPS2, EXPO, BRIDGE>;
+            case FC_BUMPS3: return k_paths<SDD_FP32_STEP, false, FC_BUMPS3, EXPO, BRIDGE>;
+            case FC_BUMPS6: return k_paths<SDD_FP32_STEP, false, FC_BUMPS6, EXPO, BRIDGE>;
+            default: return k_paths<SDD_FP32_STEP, false, FC_ANY, EXPO, BRIDGE>;
         }
     }
     switch (fc) {
-        case FC_RING: return k_paths<SDD_FP32_STEP, true, FC_RING, EXPO>;
-        case FC_RIDGE: return k_paths<SDD_FP32_STEP, true, FC_RIDGE, EXPO>;
-        case FC_TABLE: return k_paths<SDD_FP32_STEP, true, FC_TABLE, EXPO>;
-        case FC_BUMPS1: return k_paths<SDD_FP32_STEP, true, FC_BUMPS1, EXPO>;
-        case FC_BUMPS2: return k_paths<SDD_FP32_STEP, true, FC_BUMPS2, EXPO>;
-        case FC_BUMPS3: return k_paths<SDD_FP32_STEP, true, FC_BUMPS3, EXPO>;
-        default: return k_paths<SDD_FP32_STEP, true, FC_BUMPS6, EXPO>;
+        case FC_RING: return k_paths<SDD_FP32_STEP, true, FC_RING, EXPO, BRIDGE>;
+        case FC_RIDGE: return k_paths<SDD_FP32_STEP, true, FC_RIDGE, EXPO, BRIDGE>;
+        case FC_TABLE: return k_paths<SDD_FP32_STEP, true, FC_TABLE, EXPO, BRIDGE>;
+        case FC_BUMPS1: return k_paths<SDD_FP32_STEP, true, FC_BUMPS1, EXPO, BRIDGE>;
+        case FC_BUMPS2: return k_paths<SDD_FP32_STEP, true, FC_BUMPS2, EXPO, BRIDGE>;
+        case FC_BUMPS3: return k_paths<SDD_FP32_STEP, true, FC_BUMPS3, EXPO, BRIDGE>;
+        default: return k_paths<SDD_FP32_STEP, true, FC_BUMPS6, EXPO, BRIDGE>;
     }
 }
 
@@ -1472,13 +1483,15 @@ static PathKernel path_kernel(int precision, bool one, int kc)
 {
     if (precision == SDD_FP64) return one ? k_paths<SDD_FP64, true, FC_ANY> : k_paths<SDD_FP64, false, FC_ANY>;
     const int fc = kc & (KC_EXPO - 1);
-    if (kc & KC_EXPO) return path_kernel_fp32<true>(one, fc);
-    return path_kernel_fp32<false>(one, fc);
+    const bool bridge = (kc & KC_BRIDGE) != 0;
+    if (kc & KC_EXPO) return bridge ? path_kernel_fp32<true, true>(one, fc) : path_kernel_fp32<true, false>(one, fc);
+    return bridge ? path_kernel_fp32<false, true>(one, fc) : path_kernel_fp32<false, false>(one, fc);
 }
 
-int mesh_kernel_class(int family, int nb, int stepper)
+int mesh_kernel_class(int family, int nb, int stepper, int exit_test)
 {
-    return fam_class(family, nb) + (stepper == SDD_STEP_EXPONENTIAL ? KC_EXPO : 0);
+    return fam_class(family, nb) + (stepper == SDD_STEP_EXPONENTIAL ? KC_EXPO : 0) +
+           (exit_test == SDD_EXIT_BRIDGE ? KC_BRIDGE : 0);
 }
 
 int mc_grid_blocks(int precision, int kc, bool one, int* blocks, int* threads)

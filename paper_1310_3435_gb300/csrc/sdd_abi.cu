@@ -451,7 +451,7 @@ int run_mc(sdd_plan* p, const sdd_mc_params* mc, double* mean_dev, double* stder
     if ((rc = mc_args(p, mc, mean_dev, stderr_dev, sums_dev, a, few, stream))) return rc;
     SDD_CUDA(cudaMemsetAsync(p->d_stats, 0, sizeof(McStatsDev), stream));
     if ((rc = launch_mc(a, mc->precision, mesh_kernel_class(a.single.family, a.single.nb,
-                                                            a.single.stepper), stream)))
+                                                            a.single.stepper, mc->exit_test), stream)))
         return rc;
     p->items_valid = true;
     p->items_mc = *mc;
@@ -1155,7 +1155,8 @@ int sdd_interface_mc_advance(sdd_plan* p, const sdd_mc_params* mc, uint64_t max_
     a.item_base = p->resume_next;
     a.total_items = end;
     if ((rc = launch_mc_paths(a, mc->precision,
-                              mesh_kernel_class(a.single.family, a.single.nb, a.single.stepper),
+                              mesh_kernel_class(a.single.family, a.single.nb, a.single.stepper,
+                                                mc->exit_test),
                               stream)))
         return rc;
     p->resume_next = end;
@@ -1658,7 +1659,8 @@ int sdd_batch_create(sdd_plan* const* plans, int n_plans, const sdd_mc_params* m
     std::vector<std::pair<int, int>> key(n_plans);
     for (int i = 0; i < n_plans; ++i) {
         const int nb = plans[i]->dens.family == SDD_FAMILY_BUMPS ? (int)plans[i]->dens.params[0] : 0;
-        key[i] = {mc[i].precision, mesh_kernel_class(plans[i]->dens.family, nb, mc[i].stepper)};
+        key[i] = {mc[i].precision, mesh_kernel_class(plans[i]->dens.family, nb, mc[i].stepper,
+                                                       mc[i].exit_test)};
     }
     std::vector<int> order(n_plans);
     for (int i = 0; i < n_plans; ++i) order[i] = i;
@@ -2195,7 +2197,8 @@ extern "C" int sdd_interface_mc_static(int n, const int32_t* nodes, int64_t n_no
     a.queue = reinterpret_cast<unsigned long long*>(b);          // zeroed by the launcher
     a.slots = reinterpret_cast<Slot*>(b + kStaticHeadBytes);     // written before read
     SDD_CUDA(cudaMemsetAsync(m.stats, 0, sizeof(McStatsDev), stream));
-    rc = launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper), stream);
+    rc = launch_mc(a, mc->precision, mesh_kernel_class(m.family, m.nb, m.stepper, mc->exit_test),
+                   stream);
     if (rc == SDD_OK) {
         std::lock_guard<std::mutex> lock(g_static_mu);
         g_static[dev].paths = mc->paths_per_node * (uint64_t)n_nodes;   // paths of all nodes

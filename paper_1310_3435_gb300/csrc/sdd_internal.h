@@ -108,10 +108,13 @@ struct McArgs {
 
 // Kernel class of a mesh for the FP32 path kernel: its density class (one
 // kernel per class; kFamAny selects the kernel that handles every class) plus
-// KC_EXPO for exponential time stepping.  FP64 stepping has one kernel.
-int mesh_kernel_class(int family, int nb, int stepper);
+// KC_EXPO for exponential time stepping and KC_BRIDGE for the Brownian-bridge
+// exit test (kernels with the test inline it; the others leave it out).
+// FP64 stepping has one kernel.
+int mesh_kernel_class(int family, int nb, int stepper, int exit_test);
 constexpr int kFamAny = 7;
 constexpr int KC_EXPO = 8;
+constexpr int KC_BRIDGE = 16;
 
 // Interpolated interface node of a few-point interface (§3.6): value =
 // (1 - w) A + w B per component, A / B the mean (and std-err) of interface
