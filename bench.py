@@ -443,6 +443,7 @@ def run_native(args):
     plan.close()
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_leg(N, count=args.count)
+        line["precision_stress"] = precision_stress_leg(N)
     if rank == 0 and not args.no_served:
         line["served"] = serve_leg(args.served_rates, args.served_count, args.served_stderr,
                                    1025, precision=W.FP32_STEP, ideal=True)
@@ -933,6 +934,36 @@ def bias_on_sample(N, specs, nodes_per_mesh=8, paths=2048):
         count += d.size
     return {"sample": "%d meshes x %d nodes x first %d paths" % (len(specs), nodes_per_mesh, paths),
             "max_abs": worst, "max_abs_over_stderr": worst_sigma, "mean_signed": signed / count}
+
+
+def precision_stress_leg(N, paths=20000, stream=None):
+    """The precision-stress workload (1025 x 1025, 8 x 8, the anisotropic
+    ridge, dt = 1e-5, FP32 stepping with FP64 sums) at a reduced N, one
+    single-mesh launch timed with CUDA events after a warm-up, with the
+    precision-induced bias on a 16-node oracle sample beside its Monte Carlo
+    error."""
+    import torch
+    spec = W.config4(paths=paths)
+    stream = stream or torch.cuda.Stream()
+    with N.Plan(spec) as P:
+        mc = P.mc_params()
+        mean = torch.zeros((P.n_nodes, 2), dtype=torch.float64, device="cuda")
+        se = torch.zeros_like(mean)
+        N.sdd_interface_mc(P.handle, P.mc_params(paths=1024), mean, se, want_stats=False,
+                           stream=stream)                                  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        N.sdd_interface_mc(P.handle, mc, mean, se, want_stats=False, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = N.sdd_plan_last_mc_stats(P.handle)
+        sec = e0.elapsed_time(e1) / 1000.0
+    return {"workload": "1025x1025 8x8 ridge w = 1 + 20 exp(-200 (t - 0.3 - 0.2 sin 2 pi s)^2), "
+                        "dt=1e-5, FP32 stepping, N=%d (the configuration's 1e6 scaled down)" % paths,
+            "interface_nodes": int(P.n_nodes), "path_steps": int(st.path_steps), "seconds": sec,
+            "path_steps_per_s": st.path_steps / sec, "max_stderr": float(st.max_stderr),
+            "non_exits": int(st.non_exits),
+            "precision_bias": bias_on_sample(N, [spec], nodes_per_mesh=16, paths=2048)}
 
 
 def mesh_quality_of(N, plan, mesh):
