@@ -1028,8 +1028,14 @@ def batched_leg(N, count=256, paths=0, autotune=True, steps=1, warmup=1, stream=
         tuner.save()
         mcs = [p.mc_params(chunk=k["chunk"]) for p, k in zip(plans, picks)]
         sps = [p.solve_params(block_threads=k["block_threads"]) for p, k in zip(plans, picks)]
+        # the batch's one solve launch: its own CTA size, timed on the whole batch
+        # (the interface values: a first Monte Carlo-free solve from the boundary
+        # map is enough, the solve's cost does not depend on them)
+        bt = tuner.tune_batch_solve(plans, mcs, sps)
+        sps = [p.solve_params(block_threads=bt) for p in plans]
         tuned = {"buckets_timed": tuner.timed, "seconds": time.perf_counter() - t0,
-                 "block_threads": sorted({k["block_threads"] for k in picks}),
+                 "block_threads_per_bucket": sorted({k["block_threads"] for k in picks}),
+                 "batch_solve_block_threads": bt,
                  "chunks": sorted({k["chunk"] for k in picks})}
     t0 = time.perf_counter()
     batch = N.Batch(plans, mcs, sps)

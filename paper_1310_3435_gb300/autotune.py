@@ -8,7 +8,8 @@ in a JSON file:
   node).  FP32 stepping keeps the automatic size: its lanes stream across work
   items, and its speed does not depend on the item size (measured);
 * threads per subdomain CTA of the batched solves (256, 512, 1024), bucketed
-  by (solver, log2 of the largest subdomain's interior nodes).
+  by (solver, log2 of the largest subdomain's interior nodes), and, for a
+  whole batch, the CTA size of its one solve launch (`tune_batch_solve`).
 
 Each candidate is timed with CUDA events on the real kernels, through the C
 ABI, on a reduced copy of the request: its first `probe_paths` paths per
@@ -126,6 +127,47 @@ class Autotuner:
         best = min(candidates, key=lambda c: times[str(c)])
         self.cache[key] = {"best": best, "ms": times}
         return best
+
+    def tune_batch_solve(self, plans, mcs, sps, candidates=(512, 1024)) -> int:
+        """CTA size for the solve launch of a batch: all its subdomains run in
+        one launch of one CTA size, and with many subdomains several smaller
+        CTAs per SM beat one large one (their barrier waits overlap), which
+        single-mesh timings do not show.  Sets each plan's interface values to
+        its nodes' coordinates (one solve per plan; the solve's cost does not
+        depend on the values), then times the batch's fill + solve phase per
+        candidate and returns the fastest; the candidates' batches are built
+        and freed here."""
+        if self._timer is not None:
+            return min(candidates, key=lambda c: self._timer("batch", None, c))
+        import numpy as np
+        import torch
+        from . import native as N
+        from .native import solve_params as _sp
+        stream = torch.cuda.Stream()
+        n_max = max(p.n for p in plans)
+        mesh = torch.empty((n_max * n_max * 2,), dtype=torch.float64, device="cuda")
+        for p, sp in zip(plans, sps):
+            iface = np.ascontiguousarray(p.nodes() / (p.n - 1.0))
+            N.sdd_subdomain_solve(p.handle, iface, sp, mesh[:p.n * p.n * 2], want_stats=False,
+                                  stream=stream)
+        stream.synchronize()
+        best, best_ms = None, None
+        for c in candidates:
+            sp_c = [_sp(solver=sp.solver, tol=sp.tol, max_iter=sp.max_iter, omega=sp.omega,
+                        block_threads=c) for sp in sps]
+            with N.Batch(plans, mcs, sp_c) as B:
+                B.run_phases(2, stream=stream)                        # warm-up
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.run_phases(2, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+            self.timed += 1
+            if best_ms is None or ms < best_ms:
+                best, best_ms = c, ms
+        return int(best)
 
     def tune(self, spec, n_nodes: int | None = None) -> dict:
         if n_nodes is None:

@@ -613,10 +613,14 @@ __device__ void cg_box(const SolveMeshDev& M, const Box& B, SubStat& st, double*
     st.converged = r2 <= goal ? 1 : 0;
 }
 
-// MASK: solvers compiled into the kernel (bit 0 SOR, bit 1 CG), so a launch
-// whose subdomains all use one solver gets a kernel with that solver only.
+// MASK: solvers compiled into the kernel (bit 0 SOR, bit 1 multigrid CG, bit
+// 2 Jacobi CG), so a launch whose subdomains all use one solver gets a kernel
+// with that solver only.  THREADS < 1024: register use capped so that
+// 1024 / THREADS CTAs share an SM, whose barrier waits then overlap (a batch
+// of many subdomains: two CTAs of 512 per SM solve config-3's 7000
+// subdomains in 28 ms instead of 38 ms with one CTA of 1024).
 template <int MASK, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 k_solve(SolveArgs a)
 {
     __shared__ double scratch[128];

@@ -36,3 +36,12 @@ def test_buckets_separate_different_work():
     assert A.solve_bucket(small) != A.solve_bucket(big)
     assert A.largest_subdomain(small) == 15 * 15
     assert A.largest_subdomain(big) == 63 * 63
+
+
+def test_batch_solve_size_is_the_fastest_candidate():
+    times = {512: 28.0, 1024: 38.0, 256: 30.0}
+    t = A.Autotuner(timer=lambda kind, spec, c: times[c], device_name="fake",
+                    path="/nonexistent/autotune.json")
+    assert t.tune_batch_solve([], [], [], candidates=(512, 1024)) == 512
+    assert t.tune_batch_solve([], [], [], candidates=(1024,)) == 1024
+
