@@ -1086,9 +1086,9 @@ def batched_leg(N, count=256, paths=0, autotune=True, steps=1, warmup=1, stream=
 
     ms_solve, node_its, _, _ = solve_phase(batch)
     # the same solves with the diagonal (Jacobi) preconditioner, for comparison
+    # (CTAs of 1024 threads, its fastest size on this batch)
     jac = N.Batch(plans, mcs, [p.solve_params(solver=W.SOLVER_CG_JACOBI_FP32_REFINE,
-                                              block_threads=sp.block_threads)
-                               for p, sp in zip(plans, sps)])
+                                              block_threads=1024) for p in plans])
     solve_phase(jac)                                  # warm-up
     ms_jac, node_its_jac, its_jac, ok_jac = solve_phase(jac)
     jac.close()
