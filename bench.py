@@ -940,7 +940,7 @@ def precision_stress_leg(N, paths=20000, stream=None):
     """The precision-stress workload (1025 x 1025, 8 x 8, the anisotropic
     ridge, dt = 1e-5, FP32 stepping with FP64 sums) at a reduced N, one
     single-mesh launch timed with CUDA events after a warm-up, with the
-    precision-induced bias on a 16-node oracle sample beside its Monte Carlo
+    precision-induced bias on a 64-node oracle sample beside its Monte Carlo
     error."""
     import torch
     spec = W.config4(paths=paths)
@@ -963,7 +963,7 @@ def precision_stress_leg(N, paths=20000, stream=None):
             "interface_nodes": int(P.n_nodes), "path_steps": int(st.path_steps), "seconds": sec,
             "path_steps_per_s": st.path_steps / sec, "max_stderr": float(st.max_stderr),
             "non_exits": int(st.non_exits),
-            "precision_bias": bias_on_sample(N, [spec], nodes_per_mesh=16, paths=2048)}
+            "precision_bias": bias_on_sample(N, [spec], nodes_per_mesh=64, paths=2048)}
 
 
 def mesh_quality_of(N, plan, mesh):
