@@ -841,12 +841,9 @@ struct Refill {
     int set;
 };
 
-#ifndef SDD_REFILL_INLINE
-#define SDD_REFILL_INLINE __noinline__
-#endif
-__device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs& a, WarpAcc& W,
-                                                  int lane, unsigned dm, unsigned idle,
-                                                  unsigned long long mesh_end)
+__device__ __forceinline__ Refill stream_refill_inl(const MeshDev& M, const McArgs& a, WarpAcc& W,
+                                                   int lane, unsigned dm, unsigned idle,
+                                                   unsigned long long mesh_end)
 {
     Refill out{0u, 0u, 0u, 0};
     const unsigned lt = (1u << lane) - 1u;
@@ -943,6 +940,16 @@ __device__ SDD_REFILL_INLINE Refill stream_refill(const MeshDev& M, const McArgs
     return out;
 }
 
+// The refill as a called function (the batch kernels and the kernels with the
+// bridge test, whose register allocation is tighter); the single-mesh kernels
+// without the test inline it (+2% on the 257 x 257 ring workload).
+__device__ __noinline__ Refill stream_refill(const MeshDev& M, const McArgs& a, WarpAcc& W,
+                                             int lane, unsigned dm, unsigned idle,
+                                             unsigned long long mesh_end)
+{
+    return stream_refill_inl(M, a, W, lane, dm, idle, mesh_end);
+}
+
 // Streams the items of mesh M starting at `first` (already taken from the
 // queue).  Returns the first item taken that is not M's (the next mesh's, or
 // >= total_items when the queue is exhausted).
@@ -1001,7 +1008,9 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
         if (need && (!EXPO || (it & 1u) == 0u)) {
             need = false;
             const unsigned idle = __ballot_sync(FULL, !active);
-            const Refill rf = stream_refill(M, a, W, lane, dm, idle, mesh_end);
+            constexpr bool kInlineRefill = !BRIDGE && std::is_same<Keys, ParamKeys>::value;
+            const Refill rf = kInlineRefill ? stream_refill_inl(M, a, W, lane, dm, idle, mesh_end)
+                                            : stream_refill(M, a, W, lane, dm, idle, mesh_end);
             dm = 0u;
             if ((rf.given >> lane) & 1u) {
                 path = rf.path;
