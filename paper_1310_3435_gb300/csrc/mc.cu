@@ -401,8 +401,11 @@ __device__ __forceinline__ int nearest_edge(R s, R t, R& tau)
 // Gobet): side m is crossed with probability p_m = exp(-d_m(x) d_m(y) / dt)
 // (noise sqrt(2) dW), decided by U_m of Philox counter (k, path, node, 1) in
 // the side order s=0, s=1, t=0, t=1 (edges 2, 3, 0, 1).  No side can be
-// crossed when every product is >= qmax = 23 dt (p < 2^-33), and then no
-// uniforms are drawn.  Returns the edge and the tangential coordinate of the
+// crossed when every product is >= qmax, and then no uniforms are drawn:
+// with FP64 uniforms (smallest 2^-33) qmax = 23 dt gives p < 1.03e-10 <
+// 2^-33; with the FP32 uniforms of uniform23 (smallest 2^-24) qmax = 16.7 dt
+// gives p <= 2^-24.09 < 2^-24.  Either way U < p is impossible there, so the
+// cut changes no decision.  Returns the edge and the tangential coordinate of the
 // exit point (mean of the step's two), or -1.
 template <typename R, class Keys>
 __device__ __forceinline__ int bridge_exit_inl(R xs, R xt, R ys, R yt, R inv_dt, R qmax,
@@ -980,8 +983,9 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
 
     const float c4dt = (float)(-4.0 * M.dt * 0.69314718055994530942);
     constexpr bool bridge = BRIDGE;          // the kernel with the test inlines it
-    const float inv_dt = (float)(1.0 / M.dt), qmax = (float)(23.0 * M.dt);
-    const float dth = (float)std::sqrt(23.0 * M.dt);
+    // bridge cut for FP32 uniforms (no U >= 2^-24 lies below exp(-16.7))
+    const float inv_dt = (float)(1.0 / M.dt), qmax = (float)(16.7 * M.dt);
+    const float dth = (float)std::sqrt(16.7 * M.dt);
     constexpr float LN2F = 0.69314718055994530942f;
     float xs = 0.f, xt = 0.f;
     uint32_t k = 0, path = 0, node = 0, nid = 0;
@@ -1070,7 +1074,7 @@ __device__ __forceinline__ unsigned long long run_stream(const MeshDev& M, const
             const float y2s = fmaf(nb, cb, as), y2t = fmaf(nb, sb, at);
             // one test for both steps: every coordinate inside (0,1), and, with
             // the bridge test, every coordinate of x, y1, y2 farther than
-            // sqrt(23 h) from the sides (no crossing probability to draw)?
+            // sqrt(qmax) from the sides (no crossing probability to draw)?
             const float lo = fminf(fminf(y1s, y1t), fminf(y2s, y2t));
             const float hi = fmaxf(fmaxf(y1s, y1t), fmaxf(y2s, y2t));
             bool fast = (lo > 0.f) & (hi < 1.f) & (k + 2u < kmax);
