@@ -46,7 +46,7 @@ OPS_PER_STEP_RING_FP32 = 30 + 4 + 9 + 21 + 4 + 6 + 2         # = 76
 OPS_EXPO_EXTRA = 15 + 2 + 3 + 1 + 1                           # = 22
 # The Brownian-bridge test adds the distance test of a step pair's three
 # points (9 per pair); with exponential steps also the pair's largest length
-# into sqrt(23 h) (3 per pair).
+# into the cut distance sqrt(16.7 h) (3 per pair).
 OPS_BRIDGE_EXTRA = 4.5
 OPS_BRIDGE_EXPO_EXTRA = 1.5
 

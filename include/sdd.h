@@ -112,7 +112,9 @@ extern "C" {
  * probability exp(-d_s(x) d_s(y) / dt) (d_s = distance to side s, noise
  * sqrt(2) dW), decided by the uniforms of Philox counter (k, path, node, 1) in
  * the side order s=0, s=1, t=0, t=1; skipped when every product is >= 23 dt
- * (probability below 2^-33); exit point: the side, with the mean of the two
+ * (probability below 2^-33, the smallest FP64 uniform), with FP32 stepping
+ * >= 16.7 dt (below 2^-24, the smallest FP32 uniform), so the skip decides
+ * nothing; exit point: the side, with the mean of the two
  * tangential coordinates.  Cuts the O(sqrt(dt)) exit bias to O(dt). */
 #define SDD_EXIT_END_OF_STEP 0
 #define SDD_EXIT_BRIDGE      1

@@ -33,9 +33,11 @@ constexpr int MC_THREADS = 256;          // threads per block of the path kernel
 // per-family FP32-stepping kernels fit 80 registers without spills at 3
 // blocks of 256, measured fastest against 4 and 2 blocks (64, 128 registers).
 // The single-mesh constant-step kernels of the ring, ridge and table
-// densities run 7 blocks of 128 instead (72 registers, 28 warps per SM
-// instead of 24): measured +0.6%, +2.3% and +6.8%; the exponential-step
-// kernel lost 1.3% that way and the batch kernels gained nothing.
+// densities run blocks of 128 instead: 8 per SM (64 registers, no spills,
+// 32 warps) without the bridge test, measured +1.2%, +4.7% and +11.3% over 3
+// blocks of 256; 7 per SM (72 registers) with the test, which spills at 64.
+// The exponential-step kernel lost 1.3% with narrow blocks and the batch
+// kernels gained nothing.
 #ifndef SDD_MC_MIN_BLOCKS_F32
 #define SDD_MC_MIN_BLOCKS_F32 3
 #endif
@@ -1219,25 +1221,26 @@ __device__ __forceinline__ int find_mesh(const uint64_t* __restrict__ off, int n
 // density class the FP32 kernel is specialised for (FC_ANY: every class).
 // EXPO: FP32 kernel with exponential time stepping (FP64 stepping reads the
 // stepper from the mesh record).
-// Launch shape of a path kernel: 7 blocks of 128 threads for the narrow
-// kernels, else MC_THREADS threads (the launcher asks path_threads).
+// Launch shape of a path kernel: blocks of 128 threads for the narrow
+// kernels (8 per SM, 7 with the bridge test), else MC_THREADS threads (the
+// launcher asks path_threads; the grid is the occupancy API's count x SMs).
 __host__ __device__ constexpr bool narrow_kernel(int prec, bool one, int fc, bool expo)
 {
     return prec == SDD_FP32_STEP && one && !expo &&
            (fc == FC_RING || fc == FC_RIDGE || fc == FC_TABLE);
 }
 
-template <int PREC, bool ONE, int FC, bool EXPO>
+template <int PREC, bool ONE, int FC, bool EXPO, bool BRIDGE>
 struct PathShape {
     static constexpr bool kNarrow = narrow_kernel(PREC, ONE, FC, EXPO);
     static constexpr int threads = kNarrow ? 128 : MC_THREADS;
     static constexpr int min_blocks = PREC == SDD_FP64 ? SDD_MC_MIN_BLOCKS_F64
-                                      : kNarrow ? 7 : SDD_MC_MIN_BLOCKS_F32;
+                                      : kNarrow ? (BRIDGE ? 7 : 8) : SDD_MC_MIN_BLOCKS_F32;
 };
 
 template <int PREC, bool ONE, int FC, bool EXPO = false, bool BRIDGE = false>
-__global__ void __launch_bounds__(PathShape<PREC, ONE, FC, EXPO>::threads,
-                                  PathShape<PREC, ONE, FC, EXPO>::min_blocks)
+__global__ void __launch_bounds__(PathShape<PREC, ONE, FC, EXPO, BRIDGE>::threads,
+                                  PathShape<PREC, ONE, FC, EXPO, BRIDGE>::min_blocks)
 k_paths(const __grid_constant__ McArgs a)
 {
     __shared__ MeshDev single;
@@ -1273,7 +1276,7 @@ k_paths(const __grid_constant__ McArgs a)
         }
     } else {
         // FP32 stepping: path streams across the items of a mesh
-        constexpr int kWarps = PathShape<PREC, ONE, FC, EXPO>::threads / 32;
+        constexpr int kWarps = PathShape<PREC, ONE, FC, EXPO, BRIDGE>::threads / 32;
         __shared__ WarpAcc wacc[kWarps];
         __shared__ uint32_t wkeys[kWarps][20];            // batch: round keys per warp
         (void)wkeys;                                      // (single mesh: kernel parameters)
