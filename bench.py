@@ -77,8 +77,8 @@ def env_rank():
 # capture of the timed launch (dram__bytes_read.sum + dram__bytes_write.sum).
 # Valid only for the kernel source it was taken on: the bench line reports
 # null traffic once the source's SHA-256 differs.
-PATH_KERNEL_TRAFFIC = {"bytes": 301056 + 256,
-                       "source_sha256": "9d7ecf234aeeac467cb26ea4c050078fe5891826df87db356ab9d0562771d8b0"}
+PATH_KERNEL_TRAFFIC = {"bytes": 803840 + 512,
+                       "source_sha256": "07474d4d0288ec637b6b0535bbccba9f6f5fc0cdf54897d7f3634b2386e0702a"}
 
 
 # FP32 (FMA) pipe and issue-slot activity of the same kernel, from one ncu
@@ -86,8 +86,8 @@ PATH_KERNEL_TRAFFIC = {"bytes": 301056 + 256,
 # chunking; sm__inst_executed_pipe_fma and smsp__issue_active, each as a share
 # of its peak over the active cycles), keyed to the kernel source like the
 # traffic: null once the source changes.
-PATH_KERNEL_COUNTERS = {"fp32_fma_pipe": 0.3638, "issue_active": 0.7509,
-                        "source_sha256": "9d7ecf234aeeac467cb26ea4c050078fe5891826df87db356ab9d0562771d8b0"}
+PATH_KERNEL_COUNTERS = {"fp32_fma_pipe": 0.3618, "issue_active": 0.7474,
+                        "source_sha256": "07474d4d0288ec637b6b0535bbccba9f6f5fc0cdf54897d7f3634b2386e0702a"}
 
 
 def _mc_source_digest():
