@@ -441,6 +441,8 @@ def run_native(args):
                                 if k in ("value", "unit", "cores", "kind", "sample")}
         line["precision_bias"] = precision_bias_leg(N, spec, sample, mc_stats.max_stderr, stream)
     plan.close()
+    if rank == 0 and not args.no_paper_stepper:
+        line["paper_stepper"] = paper_stepper_leg(N, spec, alu_peak, stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_leg(N, count=args.count)
         line["precision_stress"] = precision_stress_leg(N)
@@ -966,6 +968,41 @@ def precision_stress_leg(N, paths=20000, stream=None):
             "precision_bias": bias_on_sample(N, [spec], nodes_per_mesh=64, paths=2048)}
 
 
+def paper_stepper_leg(N, spec, alu_peak, stream, lam=1e4, reps=3):
+    """The paper's own stepper on the timed geometry: exponential time
+    stepping at lambda = 1e4 (mean step 1e-4) with the Brownian-bridge
+    boundary test, FP32 stepping with FP64 sums, the same N.  One warm-up
+    launch, then the median of `reps` CUDA-event timed launches of the
+    interface Monte Carlo; its ALU roofline at the stepper's operation count."""
+    import torch
+    ps = W.MeshSpec(**{**spec.__dict__, "stepper": W.STEP_EXPONENTIAL,
+                       "exit_test": W.EXIT_BRIDGE, "dt": 1.0 / lam})
+    with N.Plan(ps) as P:
+        mc = P.mc_params()
+        N.sdd_interface_mc(P.handle, mc, want_stats=False, stream=stream)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            N.sdd_interface_mc(P.handle, mc, want_stats=False, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = N.sdd_plan_last_mc_stats(P.handle)
+    t = sorted(ms)[len(ms) // 2] / 1000.0
+    ops = ops_per_step(ps.stepper, ps.exit_test, ps.family)
+    achieved = ops * st.path_steps / t / 1e9
+    return {"workload": "%dx%d %dx%d ring N=%d, exponential steps lambda=%g (mean step %g), "
+                        "Brownian-bridge test" % (ps.n, ps.n, ps.sx, ps.sy, ps.paths, lam, ps.dt),
+            "path_steps_per_s": st.path_steps / t, "ms_interface_mc": 1000.0 * t,
+            "steps_per_path": st.path_steps / max(st.paths, 1),
+            "max_stderr": float(st.max_stderr), "non_exits": int(st.non_exits),
+            "l2": "not flushed (a launch reads under 1 MB of tables and node lists)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                         "unit": "Gop/s", "frac": achieved / alu_peak,
+                         "ops_per_path_step": ops}}
+
+
 def mesh_quality_of(N, plan, mesh):
     """Q_max, Q_mean and folded cells of a generated mesh (k_quality)."""
     q = N.sdd_mesh_quality(plan.handle, mesh)
@@ -1227,6 +1264,8 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-paths", type=int, default=2048,
                     help="paths per node of the plain-FP64 GPU comparison leg")
+    ap.add_argument("--no-paper-stepper", action="store_true",
+                    help="leave the exponential-stepper (lambda = 1e4, bridge) leg out of the line")
     ap.add_argument("--no-batched", action="store_true",
                     help="leave the batched (256 uneven meshes) leg out of the line")
     ap.add_argument("--no-served", action="store_true",
