@@ -128,6 +128,48 @@ def test_ring_workload_sampled_nodes_match_the_oracle(orc):
     assert rel < 2e-3
 
 
+def test_paper_stepper_at_full_size_matches_the_oracle_on_sampled_nodes(orc):
+    """The bench's paper-stepper leg as it is timed: the 257 x 257 ring,
+    4 x 4, N = 1e5, exponential steps at lambda = 1e4 with the bridge test,
+    FP32 stepping, one single-mesh launch.  Two nodes, one on the ring's
+    steep flank and one inside it, against the FP64 oracle on the same 1e5
+    Philox streams (run in path ranges over the host cores): the paired
+    difference within half a standard error, step counts within 1e-3."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1310_3435_gb300 import native as N
+    spec = _expo(W.config2(dt=1e-4))
+    assert spec.paths == 100000
+    with gpu_plan(spec) as P:
+        g = N.sdd_interface_mc_sums(P.handle, P.mc_params())
+        nodes = P.nodes()
+    r = np.hypot(nodes[:, 0] / 256.0 - 0.5, nodes[:, 1] / 256.0 - 0.5)
+    pick = [int(np.argmin(np.abs(r - 0.27))), int(np.argmin(np.abs(r - 0.12)))]
+    E = orc.bmap_tables(spec.n, spec.bmap_mode, spec.family, spec.coef_mode, spec.params)
+    parts = 16
+    per = spec.paths // parts
+
+    def run(job):
+        k, q = job
+        return orc.mc_nodes(spec.n, nodes[[k]], E, spec.family, spec.coef_mode, spec.params,
+                            seed=spec.seed, paths=per, dt=spec.dt, max_steps=spec.cap(),
+                            tie_delta=spec.tie(), node_ids=[k], threads=1, path_begin=q * per,
+                            exit_test=spec.exit_test, stepper=spec.stepper)
+
+    jobs = [(k, q) for k in pick for q in range(parts)]
+    with ThreadPoolExecutor(max_workers=orc.default_threads()) as ex:
+        outs = list(ex.map(run, jobs))
+    for a, k in enumerate(pick):
+        mine = outs[a * parts:(a + 1) * parts]
+        S = sum(o["S_all"][0] for o in mine)
+        Q = sum(o["Q_all"][0] for o in mine)
+        steps = sum(int(o["steps"][0]) for o in mine)
+        mo, so = orc.mc_estimate(nodes[[k]], spec.n, S[None, :], Q[None, :], [spec.paths])
+        mg, _ = gpu_means(g[[k]], spec.n, nodes[[k]])
+        assert np.all(np.abs(mg - mo) <= 0.5 * so), (k, mg, mo, so)
+        assert int(g["paths"][k]) == spec.paths
+        assert abs(int(g["steps"][k]) - steps) / steps < 1e-3
+
+
 def test_unknown_stepper_is_rejected():
     from paper_1310_3435_gb300 import native as N
     spec = W.small_parity_cases()[1]
