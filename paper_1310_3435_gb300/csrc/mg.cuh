@@ -121,25 +121,36 @@ struct Fine {
 // sum over the fine nodes f of the node's hat function (weight w_f) and their
 // stencil neighbours g (A_fg) of w_f A_fg P(g, J') for the coarse nodes J'
 // around (I, J).  Fine: the five-point level 0 (FINE = true) or a nine-point
-// level F.
-template <bool FINE>
-__device__ void galerkin_node(const Fine& f0, const MgLevel& F, const MgLevel& C, int I, int J,
-                              float out[9])
+// level F.  CX, CY: whether C halves the x / y side of F.  Every offset is a
+// compile-time constant once the loops are unrolled, so each term lands in a
+// fixed entry of `out`, in the order f, g, J' (row by row); only the bounds
+// (fine nodes and g inside the interior, J' a coarse interior node) are
+// tested at run time.
+template <bool FINE, int CX, int CY>
+__device__ __forceinline__ void galerkin_node(const Fine& f0, const MgLevel& F, const MgLevel& C,
+                                              int I, int J, float out[9])
 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) out[k] = 0.f;
     const int fnx = FINE ? f0.nx : F.nx, fny = FINE ? f0.ny : F.ny;
-    const int ci = C.cx ? 2 * I : I, cj = C.cy ? 2 * J : J;       // the node on the fine level
+    const int ci = CX ? 2 * I : I, cj = CY ? 2 * J : J;          // the node on the fine level
+    bool cok[9];                                                 // coarse neighbour exists
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+        const int Ip = I + d % 3 - 1, Jp = J + d / 3 - 1;
+        cok[d] = Ip >= 1 && Ip <= C.nx && Jp >= 1 && Jp <= C.ny;
+    }
+#pragma unroll
     for (int b = -1; b <= 1; ++b) {
-        const float wb = pw(b, C.cy);
+        const float wb = pw(b, CY);
         if (wb == 0.f) continue;
         const int fj = cj + b;
-        if (fj < 1 || fj > fny) continue;
+#pragma unroll
         for (int a = -1; a <= 1; ++a) {
-            const float wa = pw(a, C.cx);
+            const float wa = pw(a, CX);
             if (wa == 0.f) continue;
             const int fi = ci + a;
-            if (fi < 1 || fi > fnx) continue;
+            if (fj < 1 || fj > fny || fi < 1 || fi > fnx) continue;
             const float wf = wa * wb;
             // the fine row of A at f: (gi, gj) offsets with value v
             float v[9];
@@ -156,27 +167,34 @@ __device__ void galerkin_node(const Fine& f0, const MgLevel& F, const MgLevel& C
             }
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                if (v[k] == 0.f) continue;
-                const int gi = fi + (k % 3) - 1, gj = fj + (k / 3) - 1;
+                if (FINE && (k == 0 || k == 2 || k == 6 || k == 8)) continue;   // five points
+                const int kx = k % 3 - 1, ky = k / 3 - 1;
+                const int gi = fi + kx, gj = fj + ky;
                 if (gi < 1 || gi > fnx || gj < 1 || gj > fny) continue;   // ring: no unknown
-                // coarse nodes whose hat function covers g
-                const int Ilo = C.cx ? (gi - 1) >> 1 : gi, Ihi = C.cx ? (gi + 1) >> 1 : gi;
-                const int Jlo = C.cy ? (gj - 1) >> 1 : gj, Jhi = C.cy ? (gj + 1) >> 1 : gj;
-                for (int Jp = Jlo; Jp <= Jhi; ++Jp) {
-                    if (Jp < 1 || Jp > C.ny) continue;
-                    const float wy = pw(gj - (C.cy ? 2 * Jp : Jp), C.cy);
-                    if (wy == 0.f) continue;
-                    for (int Ip = Ilo; Ip <= Ihi; ++Ip) {
-                        if (Ip < 1 || Ip > C.nx) continue;
-                        const float wx = pw(gi - (C.cx ? 2 * Ip : Ip), C.cx);
-                        if (wx == 0.f) continue;
-                        const int dI = Ip - I, dJ = Jp - J;               // in [-1, 1]
-                        out[(dJ + 1) * 3 + dI + 1] += wf * v[k] * wx * wy;
-                    }
+                const float fv = wf * v[k];
+#pragma unroll
+                for (int d = 0; d < 9; ++d) {
+                    const int dI = d % 3 - 1, dJ = d / 3 - 1;
+                    // offset of g from coarse node (I + dI, J + dJ) on the fine level
+                    const int ox = CX ? a + kx - 2 * dI : a + kx - dI;
+                    const int oy = CY ? b + ky - 2 * dJ : b + ky - dJ;
+                    const float wx = pw(ox, CX), wy = pw(oy, CY);
+                    if (wx == 0.f || wy == 0.f) continue;
+                    if (cok[d]) out[d] += fv * wx * wy;
                 }
             }
         }
     }
+}
+
+template <bool FINE>
+__device__ __forceinline__ void galerkin_node_any(const Fine& f0, const MgLevel& F,
+                                                  const MgLevel& C, int I, int J, float out[9])
+{
+    if (C.cx && C.cy) galerkin_node<FINE, 1, 1>(f0, F, C, I, J, out);
+    else if (C.cx) galerkin_node<FINE, 1, 0>(f0, F, C, I, J, out);
+    else if (C.cy) galerkin_node<FINE, 0, 1>(f0, F, C, I, J, out);
+    else galerkin_node<FINE, 0, 0>(f0, F, C, I, J, out);
 }
 
 // Builds every coarse level's Galerkin stencil and clears its x planes
@@ -190,8 +208,8 @@ __device__ void mg_setup(const Fine& f0, float* base, const MgShape& S)
         for (int t = threadIdx.x; t < C.nx * C.ny; t += blockDim.x) {
             const int I = 1 + t % C.nx, J = 1 + t / C.nx;
             float st[9];
-            if (l == 1) galerkin_node<true>(f0, F, C, I, J, st);
-            else galerkin_node<false>(f0, F, C, I, J, st);
+            if (l == 1) galerkin_node_any<true>(f0, F, C, I, J, st);
+            else galerkin_node_any<false>(f0, F, C, I, J, st);
             const int q = C.idx(I, J);
 #pragma unroll
             for (int k = 0; k < 9; ++k) C.a[k * C.plane + q] = st[k];
