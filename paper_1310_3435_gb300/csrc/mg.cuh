@@ -298,7 +298,9 @@ __device__ void mg_prolong9(const MgLevel& F, const MgLevel& C)
 }
 
 // The coarsest level (at most MG_COARSEST nodes): `sweeps` damped Jacobi
-// sweeps from x = 0 by warp 0, one node per lane.
+// sweeps from x = 0 by warp 0, one node per lane.  The iterate stays in
+// registers and each sweep reads the neighbours' values by warp shuffles (a
+// neighbour on the ring reads 0); only the result goes to memory.
 __device__ void mg_coarsest(const MgLevel& L, int sweeps)
 {
     if (threadIdx.x < 32) {
@@ -307,33 +309,40 @@ __device__ void mg_coarsest(const MgLevel& L, int sweeps)
         const int I = mine ? 1 + lane % L.nx : 1, J = mine ? 1 + lane / L.nx : 1;
         const int q = L.idx(I, J);
         float a[9];
+        int src[9];
+        bool in[9];
         float2 b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int In = I + k % 3 - 1, Jn = J + k / 3 - 1;
+            in[k] = mine && In >= 1 && In <= L.nx && Jn >= 1 && Jn <= L.ny;
+            src[k] = in[k] ? (In - 1) + (Jn - 1) * L.nx : lane;
+        }
         if (mine) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) a[k] = L.a[k * L.plane + q];
             b = L.b[q];
-            L.x[q] = make_float2(0.f, 0.f);
         } else {
 #pragma unroll
             for (int k = 0; k < 9; ++k) a[k] = 0.f;
             a[4] = 1.f;
         }
         const float w = 0.8f / a[4];
-        __syncwarp();
+        float2 x = make_float2(0.f, 0.f);
         for (int s = 0; s < sweeps; ++s) {
             float2 r = b;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-                if (!mine) break;
-                const float2 v = L.x[q + ((k / 3) - 1) * L.pitch + (k % 3) - 1];
+                float2 v;
+                v.x = __shfl_sync(0xffffffffu, x.x, src[k]);
+                v.y = __shfl_sync(0xffffffffu, x.y, src[k]);
+                if (!in[k]) v = make_float2(0.f, 0.f);
                 r.x -= a[k] * v.x;
                 r.y -= a[k] * v.y;
             }
-            float2 x = mine ? L.x[q] : make_float2(0.f, 0.f);
-            __syncwarp();
-            if (mine) L.x[q] = make_float2(x.x + w * r.x, x.y + w * r.y);
-            __syncwarp();
+            if (mine) x = make_float2(x.x + w * r.x, x.y + w * r.y);
         }
+        if (mine) L.x[q] = x;
     }
     __syncthreads();
 }
