@@ -90,6 +90,15 @@ PATH_KERNEL_COUNTERS = {"fp32_fma_pipe": 0.3618, "issue_active": 0.7474,
                         "source_sha256": "07474d4d0288ec637b6b0535bbccba9f6f5fc0cdf54897d7f3634b2386e0702a"}
 
 
+# The same counters for the kernel of the paper's stepper (exponential steps at
+# lambda = 1e4 with the bridge test, the bench geometry), from one ncu capture
+# at N = 16384 (same kernel and launch shape), with the share of lanes active
+# per issued instruction (smsp__thread_inst_executed_per_inst_executed / 32).
+PAPER_STEPPER_COUNTERS = {"fp32_fma_pipe": 0.3102, "issue_active": 0.7334,
+                          "lanes_active": 21.86 / 32,
+                          "source_sha256": "07474d4d0288ec637b6b0535bbccba9f6f5fc0cdf54897d7f3634b2386e0702a"}
+
+
 def _mc_source_digest():
     import hashlib
     src = os.path.join(ROOT, "paper_1310_3435_gb300", "csrc", "mc.cu")
@@ -992,6 +1001,9 @@ def paper_stepper_leg(N, spec, alu_peak, stream, lam=1e4, reps=3):
     t = sorted(ms)[len(ms) // 2] / 1000.0
     ops = ops_per_step(ps.stepper, ps.exit_test, ps.family)
     achieved = ops * st.path_steps / t / 1e9
+    c = PAPER_STEPPER_COUNTERS
+    known = (ps.n, ps.sx, ps.family, ps.paths) == (257, 4, W.FAMILY_RING, 100000) and \
+        _mc_source_digest() == c["source_sha256"]
     return {"workload": "%dx%d %dx%d ring N=%d, exponential steps lambda=%g (mean step %g), "
                         "Brownian-bridge test" % (ps.n, ps.n, ps.sx, ps.sy, ps.paths, lam, ps.dt),
             "path_steps_per_s": st.path_steps / t, "ms_interface_mc": 1000.0 * t,
@@ -1000,7 +1012,12 @@ def paper_stepper_leg(N, spec, alu_peak, stream, lam=1e4, reps=3):
             "l2": "not flushed (a launch reads under 1 MB of tables and node lists)",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "Gop/s", "frac": achieved / alu_peak,
-                         "ops_per_path_step": ops}}
+                         "ops_per_path_step": ops,
+                         "fp32_fma_pipe_frac_ncu": c["fp32_fma_pipe"] if known else None,
+                         "issue_frac_ncu": c["issue_active"] if known else None,
+                         "lanes_active_frac_ncu": c["lanes_active"] if known else None,
+                         "pipe_basis": "ncu of the kernel source at N = 16384; null if the "
+                                       "source or the geometry changed"}}
 
 
 def mesh_quality_of(N, plan, mesh):
