@@ -368,6 +368,24 @@ __device__ __forceinline__ void fine_rb(const Fine& f, const Work& W, int colour
     __syncthreads();
 }
 
+// The cycle's first red sweep, from z = 0: every black neighbour is still
+// zero, so the update is z = (r + 0) / (sum c), read from r and the diagonal
+// alone (the + 0 turns a -0 into +0, as adding the zero products does).
+__device__ __forceinline__ void fine_red_from_zero(const Fine& f, const Work& W)
+{
+    const int hx = (f.nx + 1) / 2;
+    for (int t = threadIdx.x; t < hx * f.ny; t += blockDim.x) {
+        const int J = 1 + t / hx;
+        const int I = 1 + ((1 + J) & 1) + 2 * (t % hx);
+        if (I > f.nx) continue;
+        const int64_t g = f.id(I, J);
+        const float2 r = W.r[g];
+        const float di = W.dinv[g];
+        W.z[g] = make_float2((r.x + 0.f) * di, (r.y + 0.f) * di);
+    }
+    __syncthreads();
+}
+
 // t = r - A z on level 0 (into the q workspace), then level 1: b = P^T t, x = 0.
 __device__ void fine_restrict(const Fine& f, const Work& W, const MgLevel& C)
 {
@@ -423,14 +441,9 @@ __device__ void fine_prolong(const Fine& f, const Work& W, const MgLevel& C)
 // z = M^-1 r: one V-cycle from z = 0.
 __device__ void mg_vcycle(const Fine& f, const Work& W, float* base, const MgShape& S)
 {
-    // pre-smoothing on level 0: red, then black.  The red update reads only
-    // black neighbours, which must be zero at the start of the cycle.
-    for (int t = threadIdx.x; t < f.nx * f.ny; t += blockDim.x) {
-        const int I = 1 + t % f.nx, J = 1 + t / f.nx;
-        if (((I + J) & 1) == 1) W.z[f.id(I, J)] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    fine_rb(f, W, 0);
+    // pre-smoothing on level 0 from z = 0: red (its black neighbours are
+    // zero, so it reads none), then black, which writes every black node
+    fine_red_from_zero(f, W);
     fine_rb(f, W, 1);
     if (S.levels > 0) {
         fine_restrict(f, W, mg_level(base, S, 1));
